@@ -1,0 +1,443 @@
+"""Seeded synthetic mesh generators for 2D unstructured hybrid (quad + triangle) meshes.
+
+This module is an INPUT GENERATOR shared by the CPU oracle tests and the CUDA path.
+It holds only topology and node placement: no flux, gradient, limiter, boundary-state
+or sweep arithmetic of the gas-kinetic method lives here.
+
+A mesh is returned as plain numpy arrays in the face/cell layout the C ABI takes:
+
+    xy          float64 [n_nodes, 2]     node coordinates
+    cell_ptr    int32   [n_cells + 1]    CSR offsets into cell_nodes
+    cell_nodes  int32   [...]            counter-clockwise node lists, one per cell
+    face_nodes  int32   [n_faces, 2]     (a, b): a->b runs counter-clockwise around the
+                                         left cell, so the right-hand normal of a->b
+                                         points out of the left cell
+    face_cells  int32   [n_faces, 2]     (left, right); right = -1 on a boundary face
+    face_bc     int32   [n_faces]        0 interior, 1 far field, 2 symmetry, 3 wall
+
+Faces are numbered in the order they are first met while scanning cells in order and,
+inside a cell, its edges in counter-clockwise order. Cells keep the generator's order;
+that order is the sweep order of the LU-SGS method (Eq. 20, j < i by index).
+
+The configurations follow the paper's workloads in kind and size (Section III: laminar
+and turbulent flat plates on hybrid meshes of 1e4-6e4 cells, an airfoil with body-fitted
+quad layers and triangles outside), with synthetic geometry since no mesh of the paper
+is available.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BC_INTERIOR, BC_FARFIELD, BC_SYMMETRY, BC_WALL = 0, 1, 2, 3
+
+
+@dataclass
+class Mesh:
+    xy: np.ndarray
+    cell_ptr: np.ndarray
+    cell_nodes: np.ndarray
+    face_nodes: np.ndarray
+    face_cells: np.ndarray
+    face_bc: np.ndarray
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.xy.shape[0])
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.cell_ptr.shape[0] - 1)
+
+    @property
+    def n_faces(self) -> int:
+        return int(self.face_nodes.shape[0])
+
+    def cell_node_list(self, c: int) -> np.ndarray:
+        return self.cell_nodes[self.cell_ptr[c]:self.cell_ptr[c + 1]]
+
+    def renumbered(self, perm: np.ndarray) -> "Mesh":
+        """Return the same mesh with cell k of the result = cell perm[k] of this one.
+
+        Faces are rebuilt from the renumbered cells, so face order and orientation follow
+        the same rule as every generated mesh."""
+        cells = [self.cell_node_list(int(c)) for c in perm]
+        m = build_mesh(self.xy, cells, _bc_from_faces(self), name=self.name)
+        m.meta = dict(self.meta)
+        return m
+
+
+def _bc_from_faces(mesh: Mesh):
+    """Boundary tags of an existing mesh, keyed by the sorted node pair."""
+    table = {}
+    for f in range(mesh.n_faces):
+        if mesh.face_cells[f, 1] < 0:
+            a, b = int(mesh.face_nodes[f, 0]), int(mesh.face_nodes[f, 1])
+            table[(min(a, b), max(a, b))] = int(mesh.face_bc[f])
+    return lambda a, b, xm, ym: table[(min(a, b), max(a, b))]
+
+
+def build_mesh(xy: np.ndarray, cells, bc_of, name: str = "") -> Mesh:
+    """Build the face list of a mesh given its nodes and CCW cell node lists.
+
+    bc_of(a, b, xm, ym) returns the boundary tag of a boundary edge a->b with midpoint
+    (xm, ym)."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    ptr = np.zeros(len(cells) + 1, dtype=np.int64)
+    for c, nodes in enumerate(cells):
+        ptr[c + 1] = ptr[c] + len(nodes)
+    flat = np.concatenate([np.asarray(n, dtype=np.int64) for n in cells]) if cells else np.zeros(0, np.int64)
+    edge_face = {}
+    fn, fc = [], []
+    for c, nodes in enumerate(cells):
+        k = len(nodes)
+        for e in range(k):
+            a, b = int(nodes[e]), int(nodes[(e + 1) % k])
+            key = (min(a, b), max(a, b))
+            f = edge_face.get(key)
+            if f is None:
+                edge_face[key] = len(fn)
+                fn.append((a, b))
+                fc.append([c, -1])
+            else:
+                if fc[f][1] != -1:
+                    raise ValueError(f"edge {key} shared by more than two cells")
+                if fn[f] != (b, a):
+                    raise ValueError(f"edge {key}: inconsistent orientation between cells")
+                fc[f][1] = c
+    face_nodes = np.asarray(fn, dtype=np.int32).reshape(-1, 2)
+    face_cells = np.asarray(fc, dtype=np.int32).reshape(-1, 2)
+    face_bc = np.zeros(face_nodes.shape[0], dtype=np.int32)
+    for f in range(face_nodes.shape[0]):
+        if face_cells[f, 1] < 0:
+            a, b = face_nodes[f]
+            xm = 0.5 * (xy[a, 0] + xy[b, 0])
+            ym = 0.5 * (xy[a, 1] + xy[b, 1])
+            face_bc[f] = bc_of(int(a), int(b), xm, ym)
+    m = Mesh(xy=xy, cell_ptr=ptr.astype(np.int32), cell_nodes=flat.astype(np.int32),
+             face_nodes=face_nodes, face_cells=face_cells, face_bc=face_bc, name=name)
+    _check_ccw(m)
+    return m
+
+
+def _check_ccw(m: Mesh) -> None:
+    """Every cell must be a simple polygon listed counter-clockwise (signed area > 0)."""
+    x = m.xy[:, 0]
+    y = m.xy[:, 1]
+    for c in range(m.n_cells):
+        nodes = m.cell_node_list(c)
+        xs, ys = x[nodes], y[nodes]
+        a = 0.5 * np.sum(xs * np.roll(ys, -1) - np.roll(xs, -1) * ys)
+        if not a > 0.0:
+            raise ValueError(f"{m.name}: cell {c} has non-positive signed area {a}")
+
+
+# --------------------------------------------------------------------------------------
+# spacing helpers
+# --------------------------------------------------------------------------------------
+
+def geometric_levels(first: float, ratio: float, n: int) -> np.ndarray:
+    """n+1 monotone coordinates starting at 0 with first spacing `first`, growth `ratio`."""
+    h = first * ratio ** np.arange(n)
+    return np.concatenate([[0.0], np.cumsum(h)])
+
+
+def _solve_ratio(first: float, total: float, n: int) -> float:
+    """Growth ratio r with first*(r^n-1)/(r-1) = total (bisection)."""
+    if abs(first * n - total) < 1e-15 * total:
+        return 1.0
+    lo, hi = (1.0 + 1e-12, 10.0) if first * n < total else (1e-6, 1.0 - 1e-12)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        s = first * (mid ** n - 1.0) / (mid - 1.0)
+        if (s < total) == (first * n < total):
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+# --------------------------------------------------------------------------------------
+# flat plate meshes (laminar and turbulent plate workloads)
+# --------------------------------------------------------------------------------------
+
+def _plate_bc(x0_wall: float = 0.0, xmin: float = -0.5, xmax: float = 1.0, ymax: float = 1.0):
+    tol = 1e-12
+
+    def bc(a, b, xm, ym):
+        if abs(ym) < tol:
+            return BC_WALL if xm >= x0_wall else BC_SYMMETRY
+        return BC_FARFIELD
+    return bc
+
+
+def flat_plate_quads(nx: int = 64, ny: int = 32, ratio: float = 1.1,
+                     xmin: float = -0.5, xmax: float = 1.0, height: float = 1.0,
+                     first: float | None = None, name: str = "plate_quads") -> Mesh:
+    """Structured nx x ny quad mesh of the laminar flat plate, stored unstructured.
+
+    x uniform on [xmin, xmax]; y geometric with `ratio` on [0, height] (or with the
+    given first spacing, the ratio then solved so the layer reaches `height`).
+    Wall on y = 0 for x >= 0, symmetry on y = 0 for x < 0, far field elsewhere."""
+    xs = np.linspace(xmin, xmax, nx + 1)
+    if first is None:
+        first = height * (ratio - 1.0) / (ratio ** ny - 1.0) if ratio != 1.0 else height / ny
+    else:
+        ratio = _solve_ratio(first, height, ny)
+    ys = geometric_levels(first, ratio, ny)
+    ys *= height / ys[-1]
+    ys[-1] = height
+    X, Y = np.meshgrid(xs, ys)  # [ny+1, nx+1]
+    xy = np.stack([X.ravel(), Y.ravel()], axis=1)
+    nid = lambda i, j: j * (nx + 1) + i
+    cells = []
+    for j in range(ny):
+        for i in range(nx):
+            cells.append([nid(i, j), nid(i + 1, j), nid(i + 1, j + 1), nid(i, j + 1)])
+    m = build_mesh(xy, cells, _plate_bc(), name=name)
+    m.meta = dict(kind="plate", nx=nx, ny=ny, first=float(first), ratio=float(ratio))
+    return m
+
+
+def flat_plate_hybrid(nx: int = 128, nq: int = 64, ntri_rows: int = 48, first: float = 1e-6,
+                      ratio: float = 1.15, xmin: float = -0.5, xmax: float = 1.0,
+                      height: float = 1.0, jitter: float = 0.25, seed: int = 1,
+                      name: str = "plate_hybrid") -> Mesh:
+    """Hybrid flat plate mesh: an nx x nq quad boundary layer (first spacing `first`,
+    growth `ratio`) topped by a jittered (nx+1) x (ntri_rows+1)-point lattice up to
+    `height`, each lattice cell split along a seeded-random diagonal into two triangles.
+
+    The lattice's bottom row is the quad layer's top row. Lattice rows grow
+    geometrically from 1.15 x the last quad height; interior lattice points are moved
+    uniformly by up to +-jitter of the local spacing; boundary points stay in place."""
+    rng = np.random.default_rng(seed)
+    xs = np.linspace(xmin, xmax, nx + 1)
+    yq = geometric_levels(first, ratio, nq)
+    top_q = yq[-1]
+    h0 = (yq[-1] - yq[-2]) * ratio
+    r2 = _solve_ratio(h0, height - top_q, ntri_rows)
+    yt = top_q + geometric_levels(h0, r2, ntri_rows)
+    yt[-1] = height
+    # node rows: quad rows 0..nq, then lattice rows 1..ntri_rows (row 0 shared)
+    ys_all = np.concatenate([yq, yt[1:]])
+    nrows = ys_all.shape[0]
+    X, Y = np.meshgrid(xs, ys_all)
+    X = X.copy()
+    Y = Y.copy()
+    dx = xs[1] - xs[0]
+    for r in range(nq + 1, nrows - 1):
+        dy_lo = ys_all[r] - ys_all[r - 1]
+        dy_hi = ys_all[r + 1] - ys_all[r]
+        for i in range(1, nx):
+            X[r, i] += jitter * dx * rng.uniform(-1.0, 1.0)
+            Y[r, i] += jitter * min(dy_lo, dy_hi) * rng.uniform(-1.0, 1.0)
+    xy = np.stack([X.ravel(), Y.ravel()], axis=1)
+    nid = lambda i, r: r * (nx + 1) + i
+    cells = []
+    for r in range(nq):
+        for i in range(nx):
+            cells.append([nid(i, r), nid(i + 1, r), nid(i + 1, r + 1), nid(i, r + 1)])
+    diag = rng.integers(0, 2, size=(ntri_rows, nx))
+    for rr in range(ntri_rows):
+        r = nq + rr
+        for i in range(nx):
+            a, b, c, d = nid(i, r), nid(i + 1, r), nid(i + 1, r + 1), nid(i, r + 1)
+            if diag[rr, i] == 0:   # split along a-c
+                cells.append([a, b, c])
+                cells.append([a, c, d])
+            else:                  # split along b-d
+                cells.append([a, b, d])
+                cells.append([b, c, d])
+    m = build_mesh(xy, cells, _plate_bc(), name=name)
+    m.meta = dict(kind="plate_hybrid", nx=nx, nq=nq, ntri_rows=ntri_rows, first=first,
+                  ratio=ratio, seed=seed)
+    return m
+
+
+# --------------------------------------------------------------------------------------
+# NACA 4-digit O-mesh (airfoil workloads)
+# --------------------------------------------------------------------------------------
+
+def naca4_surface(m: float, p: float, t: float, n_around: int) -> np.ndarray:
+    """Closed-trailing-edge NACA 4-digit section, n_around points starting at the
+    trailing edge, along the lower surface to the leading edge and back along the upper
+    surface (clockwise around the body; cosine clustering)."""
+    half = n_around // 2
+    beta = np.linspace(0.0, math.pi, half + 1)
+    xc = 0.5 * (1.0 - np.cos(beta))  # 0 (LE) .. 1 (TE)
+    yt = 5.0 * t * (0.2969 * np.sqrt(xc) - 0.1260 * xc - 0.3516 * xc ** 2
+                    + 0.2843 * xc ** 3 - 0.1036 * xc ** 4)
+    if m > 0.0 and p > 0.0:
+        yc = np.where(xc < p, m / p ** 2 * (2 * p * xc - xc ** 2),
+                      m / (1 - p) ** 2 * ((1 - 2 * p) + 2 * p * xc - xc ** 2))
+        dyc = np.where(xc < p, 2 * m / p ** 2 * (p - xc), 2 * m / (1 - p) ** 2 * (p - xc))
+    else:
+        yc = np.zeros_like(xc)
+        dyc = np.zeros_like(xc)
+    th = np.arctan(dyc)
+    xu, yu = xc - yt * np.sin(th), yc + yt * np.cos(th)
+    xl, yl = xc + yt * np.sin(th), yc - yt * np.cos(th)
+    # TE -> lower surface -> LE -> upper surface
+    lower = np.stack([xl[::-1], yl[::-1]], axis=1)      # TE .. LE
+    upper = np.stack([xu[1:-1], yu[1:-1]], axis=1)      # after LE .. before TE
+    pts = np.concatenate([lower, upper], axis=0)
+    pts[0] = (1.0, 0.0)
+    return pts[:n_around]
+
+
+def naca_omesh(m: float = 0.0, p: float = 0.0, t: float = 0.12, n_around: int = 320,
+               n_quad: int = 48, first: float = 1e-6, ratio: float = 1.2,
+               n_rings: int = 70, r_far: float = 20.0, jitter: float = 0.25,
+               seed: int = 3, name: str = "naca_omesh") -> Mesh:
+    """Hybrid O-mesh around a NACA 4-digit section: n_around x n_quad body-fitted quad
+    layers (first spacing `first`, growth `ratio`), then n_rings rings out to a circle of
+    radius r_far centred at (0.5, 0), the ring cells split into seeded-random triangles
+    and interior ring points jittered by up to +-jitter of the local spacing."""
+    rng = np.random.default_rng(seed)
+    surf = naca4_surface(m, p, t, n_around)
+    n = surf.shape[0]
+    # the surface runs clockwise around the body (TE, lower surface, LE, upper surface),
+    # so the fluid lies to the left of the centred tangent: left normal = into the fluid
+    tang = np.roll(surf, -1, axis=0) - np.roll(surf, 1, axis=0)
+    tang /= np.linalg.norm(tang, axis=1, keepdims=True)
+    nrm = np.stack([-tang[:, 1], tang[:, 0]], axis=1)
+    offs = geometric_levels(first, ratio, n_quad)
+    layers = [surf + o * nrm for o in offs]
+    inner = layers[-1]
+    h_last = offs[-1] - offs[-2]
+    # ring blend parameter from the quad top to the far circle
+    ang = np.zeros(n)
+    # far-field angles follow the surface parameter: TE at angle 0, LE at pi
+    half = n // 2
+    ang[:half + 1] = -np.linspace(0.0, math.pi, half + 1)        # lower: 0 .. -pi
+    ang[half + 1:] = np.linspace(math.pi, 0.0, n - half + 1)[1:-1]  # upper: pi .. 0
+    far = np.stack([0.5 + r_far * np.cos(ang), r_far * np.sin(ang)], axis=1)
+    dist = np.linalg.norm(far - inner, axis=1).mean()
+    r2 = _solve_ratio(h_last * ratio, dist, n_rings)
+    s = geometric_levels(h_last * ratio, r2, n_rings)
+    s /= s[-1]
+    rings = [inner + sk * (far - inner) for sk in s[1:]]
+    rings[-1] = far
+    # jitter interior ring points (not the quad top, not the far circle)
+    for k in range(len(rings) - 1):
+        prev = inner if k == 0 else rings[k - 1]
+        nxt = rings[k + 1]
+        rad = np.minimum(np.linalg.norm(rings[k] - prev, axis=1),
+                         np.linalg.norm(nxt - rings[k], axis=1))
+        tangl = np.minimum(np.linalg.norm(rings[k] - np.roll(rings[k], 1, axis=0), axis=1),
+                           np.linalg.norm(np.roll(rings[k], -1, axis=0) - rings[k], axis=1))
+        lim = jitter * np.minimum(rad, tangl)
+        rings[k] = rings[k] + lim[:, None] * rng.uniform(-1.0, 1.0, size=(n, 2)) / math.sqrt(2.0)
+    all_layers = layers + rings
+    xy = np.concatenate(all_layers, axis=0)
+    nid = lambda i, l: l * n + (i % n)
+    cells = []
+    for l in range(n_quad):
+        for i in range(n):
+            # i -> i+1 along layer l has layer l+1 on its left: CCW cell
+            cells.append([nid(i, l), nid(i + 1, l), nid(i + 1, l + 1), nid(i, l + 1)])
+    diag = rng.integers(0, 2, size=(n_rings, n))
+    for k in range(n_rings):
+        l = n_quad + k
+        for i in range(n):
+            a, b, c, d = nid(i, l), nid(i + 1, l), nid(i + 1, l + 1), nid(i, l + 1)
+            if diag[k, i] == 0:
+                cells.append([a, b, c])
+                cells.append([a, c, d])
+            else:
+                cells.append([a, b, d])
+                cells.append([b, c, d])
+    wall_nodes = n  # nodes 0..n-1 are on the body
+
+    def bc(a, b, xm, ym):
+        if a < wall_nodes and b < wall_nodes:
+            return BC_WALL
+        return BC_FARFIELD
+    mesh = build_mesh(xy, cells, bc, name=name)
+    mesh.meta = dict(kind="naca", m=m, p=p, t=t, n_around=n_around, n_quad=n_quad,
+                     n_rings=n_rings, first=first, ratio=ratio, seed=seed)
+    return mesh
+
+
+# --------------------------------------------------------------------------------------
+# small meshes for unit checks
+# --------------------------------------------------------------------------------------
+
+def tiny_quads(nx: int = 2, ny: int = 2, skew: float = 0.0, seed: int = 0,
+               bcs=("wall", "farfield")) -> Mesh:
+    """nx x ny quads on [0,1]^2 (optionally with jittered interior nodes). Bottom edge
+    is wall (or symmetry), the rest far field."""
+    rng = np.random.default_rng(seed)
+    xs = np.linspace(0.0, 1.0, nx + 1)
+    ys = np.linspace(0.0, 1.0, ny + 1)
+    X, Y = np.meshgrid(xs, ys)
+    X = X.copy(); Y = Y.copy()
+    if skew > 0:
+        for j in range(1, ny):
+            for i in range(1, nx):
+                X[j, i] += skew / nx * rng.uniform(-1, 1)
+                Y[j, i] += skew / ny * rng.uniform(-1, 1)
+    xy = np.stack([X.ravel(), Y.ravel()], axis=1)
+    nid = lambda i, j: j * (nx + 1) + i
+    cells = [[nid(i, j), nid(i + 1, j), nid(i + 1, j + 1), nid(i, j + 1)]
+             for j in range(ny) for i in range(nx)]
+    bottom = {"wall": BC_WALL, "symmetry": BC_SYMMETRY, "farfield": BC_FARFIELD}[bcs[0]]
+    other = {"wall": BC_WALL, "symmetry": BC_SYMMETRY, "farfield": BC_FARFIELD}[bcs[1]]
+    return build_mesh(xy, cells, lambda a, b, xm, ym: bottom if abs(ym) < 1e-12 else other,
+                      name=f"tiny_quads_{nx}x{ny}")
+
+
+def triangle_fan(n: int = 4, radius: float = 1.0) -> Mesh:
+    """n triangles around a centre node; the outer edges are far field."""
+    ang = np.linspace(0.0, 2 * math.pi, n, endpoint=False) + 0.3
+    xy = np.concatenate([[[0.0, 0.0]], np.stack([radius * np.cos(ang), radius * np.sin(ang)], 1)])
+    cells = [[0, 1 + k, 1 + (k + 1) % n] for k in range(n)]
+    return build_mesh(xy, cells, lambda a, b, xm, ym: BC_FARFIELD, name=f"fan{n}")
+
+
+def mixed_polygons(seed: int = 0) -> Mesh:
+    """A small mesh mixing a quad row, a pentagon, a hexagon and triangles: the
+    general-polygon cells the hybrid meshes of the paper contain. Bottom is wall,
+    the rest far field."""
+    xy = np.array([
+        [0.0, 0.0], [1.0, 0.0], [2.0, 0.0], [3.0, 0.0],      # 0..3 bottom
+        [0.0, 1.0], [1.0, 1.0], [2.0, 1.0], [3.0, 1.0],      # 4..7
+        [1.5, 1.2],                                           # 8 (pentagon apex)
+        [0.0, 2.0], [1.0, 2.2], [2.0, 2.2], [3.0, 2.0],      # 9..12
+        [2.5, 1.6],                                           # 13 (hexagon side)
+    ], dtype=np.float64)
+    cells = [
+        [0, 1, 5, 4],            # quad
+        [1, 2, 6, 8, 5],         # pentagon
+        [2, 3, 7, 6],            # quad
+        [4, 5, 10, 9],           # quad
+        [5, 8, 11, 10],          # quad
+        [6, 7, 12, 13],          # quad
+        [8, 6, 13, 11],          # quad
+        [13, 12, 11],            # triangle
+    ]
+    return build_mesh(xy, cells, lambda a, b, xm, ym: BC_WALL if abs(ym) < 1e-12 else BC_FARFIELD,
+                      name="mixed_polygons")
+
+
+# --------------------------------------------------------------------------------------
+# named workloads
+# --------------------------------------------------------------------------------------
+
+def laminar_plate() -> Mesh:
+    """Laminar flat plate: 64 x 32 quads, y ratio 1.1 (2048 cells)."""
+    return flat_plate_quads(64, 32, 1.1, name="laminar_plate_64x32")
+
+
+def turbulent_plate(seed: int = 1) -> Mesh:
+    """Turbulent flat plate: 128 x 64 quad layer + 128 x 48 x 2 triangles (20480 cells)."""
+    return flat_plate_hybrid(seed=seed, name="turbulent_plate_20480")
+
+
+def naca0012(seed: int = 3) -> Mesh:
+    """NACA 0012 hybrid O-mesh, 320 x 48 quads + 320 x 70 x 2 triangles (60160 cells)."""
+    return naca_omesh(0.0, 0.0, 0.12, seed=seed, name="naca0012_60160")
