@@ -1,0 +1,289 @@
+"""Benchmark of the IGKS hot path on GB300: cell-updates/s of full implicit iterations
+(ghosts, spectral radius, gradients, gas-kinetic flux with SA terms, residual, norms,
+both LU-SGS sweeps and the update) on a synthetic hybrid mesh.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl igks|reference]
+                  [--precision fp64|mixed] [--workload turbulent_plate|laminar_plate|naca0012]
+
+One step = one iteration of the whole hot path over one steady solve of the workload.
+`value` is device time (CUDA events on the library's stream around each step, L2 flushed
+between steps by writing a 256 MiB buffer outside the timed intervals); `e2e` is the same
+metric through the public API with host buffers: each step copies the state in from
+pinned host memory, iterates once (reading the per-solve status back) and copies the state
+out. Under torchrun each rank runs an independent replica (the method does not shard;
+replicas only) and rank 0 prints one JSON line with the max time over ranks.
+--impl reference times the CPU oracle (single thread) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from igks_inputs import fields as F  # noqa: E402
+from igks_inputs import meshgen as G  # noqa: E402
+
+WORKLOADS = {
+    "turbulent_plate": (G.turbulent_plate, F.turbulent_plate_flow,
+                        "turbulent flat plate, SA, Ma 0.2, Re 5e6, 128x64 quads + 12288 triangles"),
+    "laminar_plate": (G.laminar_plate, F.laminar_plate_flow,
+                      "laminar flat plate, Ma 0.15, Re 1e5, 64x32 quads"),
+    "naca0012": (G.naca0012, F.naca_flow, "NACA 0012, SA, Ma 0.15, Re 6e6, AoA 10, hybrid O-mesh"),
+}
+METRIC = "cell-updates/s"
+
+# Algorithmic traffic per unit of each kernel (FP64 path): every array a kernel needs is
+# streamed once; neighbour re-reads are assumed to hit in cache. Units: cells or faces.
+# (bytes per unit, unit)
+ALG_BYTES = {
+    "k_gradient": (5 * 8 + 2 * 8 + 8 * 4 + 2 * 8 + (8 + 4) * 8 + 3 * 8, "cell"),
+    "k_flux": (2 * 4 + 9 * 8 + 2 * (5 + 12 + 2 + 2) * 8 + 10 * 8, "face"),
+    "k_residual": (8 + 6 * 8 + 5 * 8 + 5 * 8 + 4 * 8, "cell"),
+    "k_sweep_fwd": (8 + 5 * 8 + 4 * 8 + 5 * 8 + 8 * 8 + 2 * 8 + 8 * 4, "cell"),
+    "k_sweep_bwd": (8 + 5 * 8 + 5 * 8 + 5 * 8 + 8 * 8 + 5 * 8 + 2 * 8 + 8 * 4, "cell"),
+}
+# FP64 flops per face of the flux kernel, from ncu's executed FP64 instruction counts
+# (2 x DFMA + DADD + DMUL) on the same kernel; see the committed flux profile summary.
+FLUX_FLOPS_PER_FACE = None
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        return dist, dist.get_rank(), ws
+    return None, 0, 1
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) >= 9 for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_baseline(mesh, flow, budget_s=15.0):
+    """The oracle as it stands, single-threaded, on the same workload (bounded sample)."""
+    import oracle as O
+    ora = O.Oracle(mesh, flow)
+    ora.iterate(1)   # first iteration (includes its own set-up costs)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        ora.iterate(1)
+        n += 1
+        if time.perf_counter() - t0 >= budget_s or n >= 200:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": mesh.n_cells * n / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{n} iterations of the {mesh.n_cells}-cell workload from a converging state, "
+                      f"{dt:.1f} s, single-threaded C oracle (-O2 -ffp-contract=off)"}
+
+
+def run_reference(args, mesh, flow, desc):
+    dist, rank, ws = _dist()
+    if rank != 0:
+        return
+    import oracle as O
+    ora = O.Oracle(mesh, flow)
+    for _ in range(args.warmup):
+        ora.iterate(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ora.iterate(1)
+    dt = time.perf_counter() - t0
+    v = mesh.n_cells * args.steps / dt
+    line = {"metric": METRIC, "value": v, "unit": METRIC, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "cells": mesh.n_cells, "faces": mesh.n_faces},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full iterations of the workload"},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="igks", choices=["igks", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="turbulent_plate", choices=list(WORKLOADS))
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    mk, fl_fn, desc = WORKLOADS[args.workload]
+    mesh, flow = mk(), fl_fn()
+    if args.impl == "reference":
+        return run_reference(args, mesh, flow, desc)
+
+    import torch
+    from paper_1709_00803_gb300 import igks
+
+    dist, rank, ws = _dist()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    prec = igks.PREC_MIXED if args.precision == "mixed" else igks.PREC_FP64
+    ctx = igks.Context(precision=prec, device=dev, stream=stream.cuda_stream, timing=1)
+    sid = ctx.mesh_upload(mesh)
+    ctx.set_flow(sid, flow)
+    ctx.init_freestream(sid)
+    info = ctx.mesh_info(sid)
+    ctx.enqueue(args.warmup)
+    stream.synchronize()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ktimes = {}
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))        # evict the solve's working set from L2
+            starts[k].record(stream)
+            ctx.enqueue(1)
+            ends[k].record(stream)
+            stream.synchronize()
+            for name, t in ctx.kernel_times().items():
+                ktimes.setdefault(name, []).append(t)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    _, st = ctx.iterate(0)
+    value = ws * mesh.n_cells * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through the public API with host buffers ----
+    W_host = torch.empty((5, mesh.n_cells), dtype=torch.float64).pin_memory().numpy()
+    ctx.get_fields(sid, out=W_host)
+    e2e_steps = max(5, min(args.steps, 50))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.set_fields(sid, W_host)          # H2D: the step's input state
+        ctx.iterate(1)                       # one iteration, per-solve status read back
+        ctx.get_fields(sid, out=W_host)      # D2H: the step's result
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": ws * mesh.n_cells * e2e_steps / e2e_s, "unit": METRIC,
+           "h2d_bytes_per_step": int(W_host.nbytes), "d2h_bytes_per_step": int(W_host.nbytes) + 48}
+
+    # ---- roofline of the dominant kernel ----
+    kmean = {k: statistics.mean(v) for k, v in ktimes.items()}
+    dom = max(kmean, key=kmean.get)
+    peaks, src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    roof = None
+    if dom == "k_flux" and FLUX_FLOPS_PER_FACE:
+        fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk x 2 flop x max clock
+        ach = FLUX_FLOPS_PER_FACE * mesh.n_faces / (kmean[dom] / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}
+    elif dom in ALG_BYTES:
+        b, unit = ALG_BYTES[dom]
+        units = mesh.n_faces if unit == "face" else mesh.n_cells
+        ach = b * units / (kmean[dom] / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": f"hbm_gbs, {src}",
+                "alg_bytes_per_unit": b, "unit_of_work": unit}
+    clocks = clk.summary()
+    out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if prec == igks.PREC_FP64 else "f64 flux/residual/update, f32 sweeps",
+           "data": "synthetic",
+           "config": {"workload": desc, "cells": mesh.n_cells, "faces": mesh.n_faces,
+                      "sweep_levels": [info["levels_fwd"], info["levels_bwd"]],
+                      "precision": args.precision, "parallelism": "replicas" if ws > 1 else "single solve",
+                      "l2": "flushed between steps (256 MiB write outside the timed intervals)"},
+           "e2e": e2e, "gpu_launches": ctx.launches_per_iteration() * args.steps,
+           "kernel_ms": {k: round(v, 5) for k, v in kmean.items()},
+           "roofline": roof, "clocks": clocks,
+           "solver_state": {"iters": st[sid]["iters"], "res_l2_rel": st[sid]["res_l2_rel"], "cfl": st[sid]["cfl"]}}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(mesh, flow, args.cpu_budget)
+        out["cpu_baseline"]["cores_available"] = os.cpu_count()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.destroy()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

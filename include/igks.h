@@ -1,0 +1,208 @@
+/*
+ * igks.h -- C ABI of libigks, the GB300 (sm_103a) implementation of the per-iteration
+ * hot path of the implicit gas-kinetic scheme (IGKS) of Pan, Zhong & Zhuo,
+ * "An Implicit Gas-Kinetic Scheme for Turbulent Flow on Unstructured Hybrid Mesh",
+ * arXiv:1709.00803.
+ *
+ * A context holds one or more steady solves ("solves"), each a 2D unstructured hybrid
+ * mesh with its own flow conditions, resident in GPU memory. One call of igks_iterate
+ * advances every live solve of the context by the same number of iterations; each
+ * iteration is the paper's steady step:
+ *   ghost cells (Section II.E) -> spectral radius and time steps (Eq. 21, 23, 24)
+ *   -> least-squares gradients and limiter (Eq. 6-10) -> gas-kinetic interface flux
+ *   (Eq. 1-14, 33-34) with the Spalart-Allmaras face terms (Eq. 28-30) -> residual and
+ *   SA source (Eq. 16, 27, 28a) -> CFL adaptation (Eq. 25) -> matrix-free LU-SGS forward
+ *   and backward sweeps (Eq. 19-22, 31-32) -> update.
+ *
+ * Conventions
+ *  - Every function returns an int status: IGKS_OK (0), IGKS_CONVERGED (1) where noted,
+ *    or a negative IGKS_E* code. igks_last_error() gives a message owned by the context.
+ *  - All array arguments are HOST pointers owned by the caller. The library copies what
+ *    it needs during the call and never keeps a caller pointer.
+ *  - Device memory belongs to the context and is released by igks_destroy.
+ *  - A context is not thread-safe; distinct contexts may be used from distinct threads.
+ *  - Index arrays are int32, zero-based. Field arrays are float64, structure-of-arrays:
+ *    component k of cell i is at [k * n_cells + i].
+ */
+#ifndef IGKS_H
+#define IGKS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IGKS_OK 0
+#define IGKS_CONVERGED 1
+#define IGKS_EINVAL (-1)    /* bad argument */
+#define IGKS_EMESH (-2)     /* mesh failed validation (index, orientation, closure) */
+#define IGKS_ENOMEM (-3)    /* device allocation failed */
+#define IGKS_ECUDA (-4)     /* CUDA runtime error */
+#define IGKS_DIVERGED (-5)  /* non-positive density/pressure or non-finite state */
+#define IGKS_TIMEOUT (-6)   /* a device wait ran out of its spin limit */
+#define IGKS_EBUSY (-7)     /* operation not allowed in the current state */
+
+/* boundary tags of face_bc (Section II.E) */
+#define IGKS_BC_INTERIOR 0
+#define IGKS_BC_FARFIELD 1  /* characteristic (Riemann-invariant) far field */
+#define IGKS_BC_SYMMETRY 2
+#define IGKS_BC_WALL 3      /* adiabatic non-slip wall */
+
+/* precision of the LU-SGS sweeps; flux, residual and state update are always FP64 */
+#define IGKS_PREC_FP64 0
+#define IGKS_PREC_MIXED 1   /* sweeps and implicit operator in FP32 */
+
+#define IGKS_LIMITER_NONE 0
+#define IGKS_LIMITER_BJ 1      /* Barth-Jespersen reading of the min-max limiter, Eq. 9 */
+#define IGKS_LIMITER_VENKAT 2  /* Venkatakrishnan's smooth variant */
+
+typedef struct igks_options {
+  int32_t precision;      /* IGKS_PREC_* */
+  int32_t device;         /* CUDA device ordinal */
+  void* stream;           /* cudaStream_t to run on, or NULL for a stream of the context */
+  int32_t check_every;    /* iterations between host checks of the stopping rule (>=1) */
+  int32_t use_graph;      /* capture one iteration as a CUDA graph and replay it */
+  int32_t sweep_threads;  /* threads per block of the sweep kernels (0: default) */
+  int32_t timing;         /* record CUDA events around every kernel (igks_kernel_times) */
+  int32_t reserved[6];
+} igks_options;
+
+/* Flow conditions of one solve. Non-dimensional: free-stream density, speed and the
+ * reference length are 1, so p_inf = 1/(gamma Ma^2), mu_inf = 1/Re; gamma = 1.4 (K = 3). */
+typedef struct igks_flow {
+  double mach, reynolds, aoa_deg;
+  double prandtl;          /* one Pr for the laminar and turbulent heat flux */
+  double t_ref, s_suth;    /* free-stream temperature and Sutherland constant [K] */
+  int32_t sa_on;           /* Spalart-Allmaras turbulence model on/off */
+  int32_t limiter;         /* IGKS_LIMITER_* */
+  double nut_ratio_inf;    /* free-stream nu_tilde / nu */
+  double cfl_exp;          /* CFL of the flux time step (Eq. 23) */
+  double cfl_init, cfl_min, cfl_max;   /* implicit CFL (Eq. 24) and Eq. 25 clamp */
+  double res_target;       /* stop at L2(M_rho/Omega) <= res_target * first-iteration value */
+  double venkat_k;         /* Venkatakrishnan limiter constant */
+  double c_num;            /* numerical collision time coefficient (pressure-jump term) */
+  int32_t visc_sr;         /* add the viscous term to the face spectral radius */
+  int32_t pad_;
+} igks_flow;
+
+typedef struct igks_status {
+  int32_t iters;           /* iterations done by this solve */
+  int32_t state;           /* 0 running, IGKS_CONVERGED, or a negative code */
+  double res_l2_rho;       /* RMS over cells of M_rho / Omega at the last iteration */
+  double res_l2_rel;       /* res_l2_rho / its first-iteration value */
+  double res_inf;          /* max |M_rho| at the last iteration (Eq. 25) */
+  double eq40_ratio;       /* max_i |dW_i| / |W_i| of the last update (Eq. 40) */
+  double cfl;              /* implicit CFL used by the last sweep */
+  double dt;               /* flux time step of the last iteration (Eq. 23) */
+} igks_status;
+
+typedef struct igks_ctx igks_ctx;
+
+/* Create an empty context on opt->device. Errors: IGKS_EINVAL, IGKS_ECUDA. */
+int igks_create(const igks_options* opt, igks_ctx** out);
+
+/* Add one solve: a mesh in face/cell form (Section II.D's mesh data reduced to nodes,
+ * cells and faces). Cells are CCW node lists (cell_ptr CSR, any polygon); face f joins
+ * nodes face_nodes[2f] -> face_nodes[2f+1], CCW around its left cell face_cells[2f];
+ * face_cells[2f+1] is the right cell or -1 on a boundary, where face_bc[f] gives the tag.
+ * The cell numbering is the sweep order of the LU-SGS method (Eq. 20, j < i).
+ * *solve_id receives the solve's index. Must precede the first igks_iterate.
+ * Errors: IGKS_EINVAL (null/negative sizes), IGKS_EMESH (index out of range, face with
+ * no left cell, non-boundary face without a right cell), IGKS_EBUSY (after iterate). */
+int igks_mesh_upload(igks_ctx* ctx, int32_t n_nodes, const double* xy /*[2*n_nodes]*/,
+                     int32_t n_cells, const int32_t* cell_ptr /*[n_cells+1]*/,
+                     const int32_t* cell_nodes, int32_t n_faces,
+                     const int32_t* face_nodes /*[2*n_faces]*/,
+                     const int32_t* face_cells /*[2*n_faces]*/,
+                     const int32_t* face_bc /*[n_faces]*/, int32_t* solve_id);
+
+/* Set the flow conditions of a solve (before its first iteration, or to restart it). */
+int igks_set_flow(igks_ctx* ctx, int32_t solve, const igks_flow* f);
+
+/* Set every cell of a solve to the free stream and reset its iteration state. Builds the
+ * device data on first use (geometry, wall distance, sweep levels are computed there;
+ * IGKS_EMESH if a cell has non-positive area or a face normal points into its left cell). */
+int igks_init_freestream(igks_ctx* ctx, int32_t solve);
+
+/* Advance every live solve by up to max_iters iterations. A solve stops on its own at
+ * convergence (res_l2_rel <= res_target) or divergence. status (nullable) receives one
+ * entry per solve. Returns IGKS_CONVERGED if every solve has converged, IGKS_OK if some
+ * are still running, IGKS_DIVERGED if any diverged, or another error. */
+int igks_iterate(igks_ctx* ctx, int32_t max_iters, igks_status* status);
+
+/* Enqueue n_iters iterations of every live solve on the context stream and return at
+ * once (no host synchronisation, no stopping check on the host; solves still stop on
+ * their own on the device). Stream-ordered with anything else the caller puts on the
+ * same stream, e.g. CUDA events for timing. */
+int igks_enqueue(igks_ctx* ctx, int32_t n_iters);
+
+/* Per-kernel device times of the most recent iteration, in launch order, measured with
+ * CUDA events recorded inside the iteration (only when the context was created with
+ * igks_options.timing = 1). ms receives up to cap entries; *n the number of kernels.
+ * igks_kernel_name(i) names entry i. Call after the stream has been synchronised. */
+int igks_kernel_times(igks_ctx* ctx, int32_t cap, float* ms, int32_t* n);
+const char* igks_kernel_name(int32_t i);
+
+/* Conserved state + nu_tilde of a solve: W[5*n_cells] SoA (rho, rho U, rho V, rho E, nu_tilde). */
+int igks_get_fields(igks_ctx* ctx, int32_t solve, double* W);
+
+/* Overwrite the state of a solve (checkpoint restore / seeded start). The iteration
+ * scalars (iteration count, CFL, previous and first residuals) are kept unless
+ * igks_set_scalars is called too. */
+int igks_set_fields(igks_ctx* ctx, int32_t solve, const double* W);
+
+/* Iteration scalars of a solve, for checkpoint/resume: out[0] iteration count,
+ * out[1] CFL, out[2] previous max|M_rho|, out[3] first-iteration L2 residual,
+ * out[4] state. igks_set_scalars takes the same layout. */
+int igks_get_scalars(igks_ctx* ctx, int32_t solve, double* out /*[5]*/);
+int igks_set_scalars(igks_ctx* ctx, int32_t solve, const double* in /*[5]*/);
+
+/* Intermediate arrays of the last iteration of a solve, for verification. `which`:
+ *  IGKS_ARR_GRAD    [4][2][n_cells] unlimited least-squares gradients (Eq. 7)
+ *  IGKS_ARR_PHI     [4][n_cells]    limiter factors (Eq. 9)
+ *  IGKS_ARR_LAMBDA_F[n_faces]       face spectral radius
+ *  IGKS_ARR_LAMBDA_C[n_cells]       per-cell sum of (Lambda_c)_ij
+ *  IGKS_ARR_FLUX    [6][n_faces]    time-integrated face flux x S (global frame) and the
+ *                                   SA face contributions to the left and right cells
+ *  IGKS_ARR_RES     [5][n_cells]    residual M (Eq. 16) and Omega Sr + R (Eq. 27)
+ *  IGKS_ARR_DWSTAR  [5][n_cells]    forward sweep result
+ *  IGKS_ARR_DW      [5][n_cells]    backward sweep result
+ *  IGKS_ARR_GHOST   [5][n_faces]    ghost states (zero on interior faces)
+ *  IGKS_ARR_GEOM_CELL[4][n_cells]   area, centroid x, centroid y, wall distance
+ *  IGKS_ARR_GEOM_FACE[5][n_faces]   length, normal x, normal y, midpoint x, midpoint y
+ * Face arrays follow the uploaded face numbering. */
+#define IGKS_ARR_GRAD 1
+#define IGKS_ARR_PHI 2
+#define IGKS_ARR_LAMBDA_F 3
+#define IGKS_ARR_LAMBDA_C 4
+#define IGKS_ARR_FLUX 5
+#define IGKS_ARR_RES 6
+#define IGKS_ARR_DWSTAR 7
+#define IGKS_ARR_DW 8
+#define IGKS_ARR_GHOST 9
+#define IGKS_ARR_GEOM_CELL 10
+#define IGKS_ARR_GEOM_FACE 11
+int igks_get_array(igks_ctx* ctx, int32_t solve, int32_t which, double* out);
+
+/* Sizes of a solve: out[0] n_cells, out[1] n_faces, out[2] forward sweep levels,
+ * out[3] backward sweep levels, out[4] boundary faces. */
+int igks_mesh_info(igks_ctx* ctx, int32_t solve, int32_t* out /*[5]*/);
+
+/* Pressure and viscous force on the faces tagged bc_tag of a solve, as lift and drag
+ * coefficients about the free-stream direction: out[0] Cl, out[1] Cd, out[2] Cd_viscous. */
+int igks_get_forces(igks_ctx* ctx, int32_t solve, int32_t bc_tag, double* out /*[3]*/);
+
+/* Number of kernel launches one iteration issues (for launch accounting). */
+int igks_launches_per_iteration(igks_ctx* ctx, int32_t* out);
+
+/* Release all device memory and the context. */
+int igks_destroy(igks_ctx* ctx);
+
+/* Message of the last error on this context (owned by the context; never NULL). */
+const char* igks_last_error(igks_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

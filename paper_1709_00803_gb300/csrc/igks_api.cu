@@ -1,0 +1,727 @@
+// igks_api.cu -- host side of libigks: the C ABI of include/igks.h.
+//
+// Holds the contexts, validates and lays out the meshes of all solves of a context in
+// one set of device buffers, builds the LU-SGS level schedule (cells grouped by their
+// depth in the dependency graph of the sequential sweep of Eq. 20), captures one
+// iteration as a CUDA graph and replays it, and copies fields in and out.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/igks.h"
+#include "igks_dev.h"
+
+using namespace igks;
+
+namespace {
+
+struct HostMesh {
+  int nn = 0, nc = 0, nf = 0;
+  std::vector<double> xy;
+  std::vector<int> cell_ptr, cell_nodes, face_nodes, face_cells, face_bc;
+  int nlev_f = 0, nlev_b = 0, nbf = 0;
+};
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct igks_ctx {
+  igks_options opt{};
+  std::vector<HostMesh> meshes;
+  std::vector<igks_flow> flows;
+  std::vector<int> flow_set;
+  bool built = false;
+  Dev dev{};
+  std::vector<Buf> bufs;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::string err = "";
+  // layout
+  std::vector<int> cell_off, cell_pad, face_off, node_off;
+  SolveState* h_st = nullptr;   // pinned mirror of the per-solve state
+  int nc_pad = 0, nf = 0, nn = 0;
+  cudaEvent_t ev[LAUNCHES_PER_ITER + 1] = {};
+};
+
+static int fail(igks_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? IGKS_ENOMEM : IGKS_ECUDA,       \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+  } while (0)
+
+
+// every copy goes through the context stream (it does not synchronise with the legacy
+// default stream); device-to-host copies wait for their data
+static cudaError_t h2d(igks_ctx* c, void* dst, const void* src, size_t n) {
+  return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, c->stream);
+}
+static cudaError_t d2h(igks_ctx* c, void* dst, const void* src, size_t n) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, c->stream);
+  return e != cudaSuccess ? e : cudaStreamSynchronize(c->stream);
+}
+static cudaError_t h2d_2d(igks_ctx* c, void* dst, size_t dpitch, const void* src, size_t spitch, size_t w, size_t h) {
+  return cudaMemcpy2DAsync(dst, dpitch, src, spitch, w, h, cudaMemcpyHostToDevice, c->stream);
+}
+static cudaError_t d2h_2d(igks_ctx* c, void* dst, size_t dpitch, const void* src, size_t spitch, size_t w, size_t h) {
+  cudaError_t e = cudaMemcpy2DAsync(dst, dpitch, src, spitch, w, h, cudaMemcpyDeviceToHost, c->stream);
+  return e != cudaSuccess ? e : cudaStreamSynchronize(c->stream);
+}
+
+static igks_flow default_flow() {
+  igks_flow f{};
+  f.mach = 0.15; f.reynolds = 1e5; f.aoa_deg = 0.0; f.prandtl = 0.72;
+  f.t_ref = 288.15; f.s_suth = 110.4; f.sa_on = 0; f.limiter = 0; f.nut_ratio_inf = 3.0;
+  f.cfl_exp = 1.0; f.cfl_init = 100.0; f.cfl_min = 100.0; f.cfl_max = 100.0;
+  f.res_target = 1e-10; f.venkat_k = 5.0; f.c_num = 1.0; f.visc_sr = 0;
+  return f;
+}
+
+static DevFlow make_devflow(const igks_flow& f) {
+  DevFlow d{};
+  const double g = GAMMA;
+  d.mach = f.mach; d.re = f.reynolds; d.prandtl = f.prandtl;
+  d.s_star = f.s_suth / f.t_ref;
+  d.lam_inf = g * f.mach * f.mach / 2.0;
+  d.mu_inf = 1.0 / f.reynolds;
+  d.nut_inf = f.sa_on ? f.nut_ratio_inf / f.reynolds : 0.0;
+  d.p_inf = 1.0 / (g * f.mach * f.mach);
+  double a = f.aoa_deg * M_PI / 180.0;
+  double u = std::cos(a), v = std::sin(a);
+  d.Winf[0] = 1.0; d.Winf[1] = u; d.Winf[2] = v;
+  d.Winf[3] = d.p_inf / (g - 1.0) + 0.5 * (u * u + v * v);
+  d.Winf[4] = d.nut_inf;
+  d.cfl_exp = f.cfl_exp; d.cfl_init = f.cfl_init; d.cfl_min = f.cfl_min; d.cfl_max = f.cfl_max;
+  d.res_target = f.res_target; d.venkat_k = f.venkat_k; d.c_num = f.c_num;
+  d.sa_on = f.sa_on; d.limiter = f.limiter; d.visc_sr = f.visc_sr;
+  return d;
+}
+
+template <class T>
+static int dalloc(igks_ctx* ctx, T** out, size_t n) {
+  void* p = nullptr;
+  size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+  CK(cudaMalloc(&p, bytes));
+  CK(cudaMemsetAsync(p, 0, bytes, ctx->stream));
+  ctx->bufs.push_back({p, bytes});
+  *out = (T*)p;
+  return 0;
+}
+
+template <class T>
+static int upload(igks_ctx* ctx, const T** out, const std::vector<T>& h) {
+  T* p;
+  int rc = dalloc(ctx, &p, h.size());
+  if (rc) return rc;
+  if (!h.empty()) CK(h2d(ctx, p, h.data(), h.size() * sizeof(T)));
+  *out = p;
+  return 0;
+}
+
+static void release(igks_ctx* ctx) {
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  ctx->gexec = nullptr;
+  ctx->graph = nullptr;
+  for (auto& b : ctx->bufs) cudaFree(b.p);
+  ctx->bufs.clear();
+  if (ctx->h_st) cudaFreeHost(ctx->h_st);
+  ctx->h_st = nullptr;
+  ctx->built = false;
+}
+
+static const char* const KERNEL_NAMES[LAUNCHES_PER_ITER] = {
+    "k_prep", "k_ghost", "k_gradient", "k_flux", "k_residual", "k_norms",
+    "k_sweep_fwd", "k_sweep_bwd", "k_end_iter"};
+
+// issue one iteration's kernels on the context stream (with an event after each kernel
+// when timing is on; event k+1 minus event k is the duration of kernel k)
+static void enqueue_iteration(igks_ctx* ctx) {
+  const Dev& d = ctx->dev;
+  cudaStream_t s = ctx->stream;
+  const int p = ctx->opt.precision, th = ctx->opt.sweep_threads;
+  const bool t = ctx->opt.timing != 0;
+  int e = 0;
+  if (t) cudaEventRecord(ctx->ev[e++], s);
+  launch_prep(d, s);                   if (t) cudaEventRecord(ctx->ev[e++], s);
+  launch_ghost(d, s);                  if (t) cudaEventRecord(ctx->ev[e++], s);
+  launch_gradient(d, s);               if (t) cudaEventRecord(ctx->ev[e++], s);
+  launch_flux(d, s);                   if (t) cudaEventRecord(ctx->ev[e++], s);
+  launch_residual(d, s);               if (t) cudaEventRecord(ctx->ev[e++], s);
+  launch_norms(d, s);                  if (t) cudaEventRecord(ctx->ev[e++], s);
+  launch_sweep_fwd(d, p, th, s);       if (t) cudaEventRecord(ctx->ev[e++], s);
+  launch_sweep_bwd(d, p, th, s);       if (t) cudaEventRecord(ctx->ev[e++], s);
+  launch_end_iter(d, s);               if (t) cudaEventRecord(ctx->ev[e++], s);
+}
+
+// dependency levels of the sequential sweep: forward uses lower neighbours, backward upper
+static void sweep_levels(const HostMesh& m, const std::vector<int>& cf_ptr, const std::vector<int>& cf_face,
+                         bool forward, std::vector<int>& order, std::vector<int>& lvl_ptr) {
+  const int n = m.nc;
+  std::vector<int> lev(n, 0);
+  int nlev = 0;
+  for (int t = 0; t < n; t++) {
+    int i = forward ? t : n - 1 - t;
+    int L = 0;
+    for (int k = cf_ptr[i]; k < cf_ptr[i + 1]; k++) {
+      int f = cf_face[k];
+      int l = m.face_cells[2 * f], r = m.face_cells[2 * f + 1];
+      if (r < 0) continue;
+      int j = (l == i) ? r : l;
+      if (forward ? (j < i) : (j > i)) L = std::max(L, lev[j] + 1);
+    }
+    lev[i] = L;
+    nlev = std::max(nlev, L + 1);
+  }
+  std::vector<int> cnt(nlev + 1, 0);
+  for (int i = 0; i < n; i++) cnt[lev[i] + 1]++;
+  for (int l = 0; l < nlev; l++) cnt[l + 1] += cnt[l];
+  lvl_ptr.assign(cnt.begin(), cnt.end());
+  order.assign(n, 0);
+  std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+  for (int t = 0; t < n; t++) {
+    int i = forward ? t : n - 1 - t;
+    order[fill[lev[i]]++] = i;
+  }
+}
+
+static int build(igks_ctx* ctx) {
+  if (ctx->built) return 0;
+  if (ctx->meshes.empty()) return fail(ctx, IGKS_EINVAL, "no mesh uploaded");
+  const int ns = (int)ctx->meshes.size();
+  CK(cudaSetDevice(ctx->opt.device));
+  // ---- layout ----
+  ctx->cell_off.assign(ns, 0); ctx->cell_pad.assign(ns, 0);
+  ctx->face_off.assign(ns, 0); ctx->node_off.assign(ns, 0);
+  int nc = 0, nf = 0, nn = 0;
+  for (int s = 0; s < ns; s++) {
+    const HostMesh& m = ctx->meshes[s];
+    ctx->cell_off[s] = nc;
+    ctx->cell_pad[s] = (m.nc + CELL_ALIGN - 1) / CELL_ALIGN * CELL_ALIGN;
+    nc += ctx->cell_pad[s];
+    ctx->face_off[s] = nf; nf += m.nf;
+    ctx->node_off[s] = nn; nn += m.nn;
+  }
+  ctx->nc_pad = nc; ctx->nf = nf; ctx->nn = nn;
+  std::vector<int> cell_solve(nc, -1), cf_ptr(nc + 1, 0), cf_face, cn_ptr(nc + 1, 0), cn_node;
+  std::vector<double> xy(2 * (size_t)nn);
+  std::vector<int> fL(nf), fR(nf), fbc(nf), fsolve(nf), fnode(2 * (size_t)nf), bface, wall_face, wall_ptr(ns + 1, 0);
+  std::vector<int> fwd_order, fwd_lvl, bwd_order, bwd_lvl, lsp(ns + 1, 0), blsp(ns + 1, 0);
+  std::vector<SolveState> st(ns);
+  std::vector<DevFlow> dfl(ns);
+  for (int s = 0; s < ns; s++) {
+    const HostMesh& m = ctx->meshes[s];
+    const int co = ctx->cell_off[s], fo = ctx->face_off[s], no = ctx->node_off[s];
+    for (int k = 0; k < m.nn; k++) {
+      xy[no + k] = m.xy[2 * k];
+      xy[nn + no + k] = m.xy[2 * k + 1];
+    }
+    // cell -> faces in ascending face order
+    std::vector<int> lp(m.nc + 1, 0), lf;
+    for (int f = 0; f < m.nf; f++) {
+      lp[m.face_cells[2 * f] + 1]++;
+      if (m.face_cells[2 * f + 1] >= 0) lp[m.face_cells[2 * f + 1] + 1]++;
+    }
+    for (int i = 0; i < m.nc; i++) lp[i + 1] += lp[i];
+    lf.assign(lp[m.nc], 0);
+    {
+      std::vector<int> fill(m.nc, 0);
+      for (int f = 0; f < m.nf; f++) {
+        int l = m.face_cells[2 * f], r = m.face_cells[2 * f + 1];
+        lf[lp[l] + fill[l]++] = f;
+        if (r >= 0) lf[lp[r] + fill[r]++] = f;
+      }
+    }
+    for (int i = 0; i < ctx->cell_pad[s]; i++) {
+      int g = co + i;
+      if (i < m.nc) {
+        cell_solve[g] = s;
+        for (int k = lp[i]; k < lp[i + 1]; k++) cf_face.push_back(fo + lf[k]);
+        for (int k = m.cell_ptr[i]; k < m.cell_ptr[i + 1]; k++) cn_node.push_back(no + m.cell_nodes[k]);
+      }
+      cf_ptr[g + 1] = (int)cf_face.size();
+      cn_ptr[g + 1] = (int)cn_node.size();
+    }
+    for (int f = 0; f < m.nf; f++) {
+      int g = fo + f;
+      fL[g] = co + m.face_cells[2 * f];
+      fR[g] = m.face_cells[2 * f + 1] >= 0 ? co + m.face_cells[2 * f + 1] : -1;
+      fbc[g] = m.face_bc[f];
+      fsolve[g] = s;
+      fnode[g] = no + m.face_nodes[2 * f];
+      fnode[nf + g] = no + m.face_nodes[2 * f + 1];
+      if (fR[g] < 0) bface.push_back(g);
+      if (fR[g] < 0 && fbc[g] == IGKS_BC_WALL) wall_face.push_back(g);
+    }
+    wall_ptr[s + 1] = (int)wall_face.size();
+    // sweep schedule
+    std::vector<int> ord, lvl;
+    sweep_levels(m, lp, lf, true, ord, lvl);
+    ctx->meshes[s].nlev_f = (int)lvl.size() - 1;
+    int base = (int)fwd_order.size();
+    for (int c : ord) fwd_order.push_back(co + c);
+    for (int p : lvl) fwd_lvl.push_back(base + p);
+    lsp[s + 1] = (int)fwd_lvl.size();
+    sweep_levels(m, lp, lf, false, ord, lvl);
+    ctx->meshes[s].nlev_b = (int)lvl.size() - 1;
+    base = (int)bwd_order.size();
+    for (int c : ord) bwd_order.push_back(co + c);
+    for (int p : lvl) bwd_lvl.push_back(base + p);
+    blsp[s + 1] = (int)bwd_lvl.size();
+    // state
+    SolveState& q = st[s];
+    std::memset(&q, 0, sizeof q);
+    q.cfl = ctx->flows[s].cfl_init;
+    q.blk_begin = co / CELL_BLOCK;
+    q.blk_end = (co + ctx->cell_pad[s]) / CELL_BLOCK;
+    q.cell_begin = co;
+    q.cell_end = co + m.nc;
+    dfl[s] = make_devflow(ctx->flows[s]);
+  }
+  // ---- device buffers ----
+  Dev& d = ctx->dev;
+  d = Dev{};
+  d.n_solves = ns; d.nc_pad = nc; d.nf = nf; d.nn = nn; d.nbf = (int)bface.size();
+  d.n_cell_blocks = nc / CELL_BLOCK;
+  int rc = 0;
+#define UP(field, vec) if ((rc = upload(ctx, &d.field, vec))) { release(ctx); return rc; }
+#define AL(field, type, n) if ((rc = dalloc(ctx, (type**)&d.field, n))) { release(ctx); return rc; }
+  UP(xy, xy); UP(cell_solve, cell_solve); UP(cf_ptr, cf_ptr); UP(cf_face, cf_face);
+  UP(cn_ptr, cn_ptr); UP(cn_node, cn_node);
+  UP(fL, fL); UP(fR, fR); UP(fbc, fbc); UP(fsolve, fsolve); UP(fnode, fnode); UP(bface, bface);
+  UP(wall_face, wall_face); UP(wall_ptr, wall_ptr);
+  UP(fwd_order, fwd_order); UP(fwd_lvl, fwd_lvl); UP(bwd_order, bwd_order); UP(bwd_lvl, bwd_lvl);
+  UP(lvl_solve_ptr, lsp); UP(blvl_solve_ptr, blsp); UP(flow, dfl);
+  AL(area, double, nc); AL(cx, double, nc); AL(cy, double, nc); AL(wall_d, double, nc);
+  AL(W, double, 5 * (size_t)nc); AL(grad, double, 8 * (size_t)nc); AL(phi, double, 4 * (size_t)nc);
+  AL(omega, double, nc); AL(mu_l, double, nc); AL(mu_t, double, nc); AL(Lam, double, nc);
+  AL(M, double, 5 * (size_t)nc); AL(fw, double, nc); AL(sa_diag, double, nc);
+  AL(dWs, double, 5 * (size_t)nc); AL(dW, double, 5 * (size_t)nc); AL(dF, double, 8 * (size_t)nc);
+  AL(fS, double, nf); AL(fnx, double, nf); AL(fny, double, nf); AL(fmx, double, nf); AL(fmy, double, nf);
+  AL(fcx, double, nf); AL(fcy, double, nf); AL(fdL, double, nf); AL(fdR, double, nf); AL(fdn, double, nf);
+  AL(lam_f, double, nf); AL(F, double, 6 * (size_t)nf); AL(sa_a, double, 4 * (size_t)nf);
+  AL(G, double, 5 * (size_t)nf); AL(Gmu, double, 2 * (size_t)nf);
+  AL(st, SolveState, ns); AL(dt_bits, unsigned long long, ns);
+  AL(part, double, 2 * (size_t)d.n_cell_blocks); AL(err, int, 4);
+#undef UP
+#undef AL
+  CK(h2d(ctx, d.st, st.data(), sizeof(SolveState) * ns));
+  std::vector<unsigned long long> inf(ns, 0x7FF0000000000000ull);
+  CK(h2d(ctx, d.dt_bits, inf.data(), sizeof(unsigned long long) * ns));
+  CK(cudaMallocHost((void**)&ctx->h_st, sizeof(SolveState) * ns));
+  // ---- geometry, validation, wall distance ----
+  launch_geometry(d, ctx->stream);
+  CK(cudaGetLastError());
+  int herr[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(herr, d.err, sizeof herr, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (herr[0] || herr[1]) {
+    release(ctx);
+    return fail(ctx, IGKS_EMESH, herr[0] ? "cell with non-positive area (cells must be CCW)"
+                                         : "face normal does not point out of its left cell");
+  }
+  launch_wall_distance(d, ctx->stream);
+  CK(cudaGetLastError());
+  // free stream everywhere
+  for (int s = 0; s < ns; s++) {
+    std::vector<double> W(5 * (size_t)ctx->cell_pad[s], 0.0);
+    for (int v = 0; v < 5; v++)
+      for (int i = 0; i < ctx->meshes[s].nc; i++) W[(size_t)v * ctx->cell_pad[s] + i] = dfl[s].Winf[v];
+    for (int v = 0; v < 5; v++)
+      CK(h2d(ctx, d.W + (size_t)v * nc + ctx->cell_off[s], W.data() + (size_t)v * ctx->cell_pad[s],
+             sizeof(double) * ctx->cell_pad[s]));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->meshes[s].nbf = 0;
+  }
+  for (int f : bface) ctx->meshes[fsolve[f]].nbf++;
+  for (int s = 0; s < ns; s++) ctx->dev.n_solves = ns;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->built = true;
+  // ---- capture one iteration ----
+  if (ctx->opt.use_graph) {
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_iteration(ctx);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &ctx->graph);
+    if (e != cudaSuccess) { release(ctx); return fail(ctx, IGKS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e)); }
+    CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
+  }
+  return 0;
+}
+
+// ===================================================================================
+// C ABI
+// ===================================================================================
+
+extern "C" {
+
+int igks_create(const igks_options* opt, igks_ctx** out) {
+  if (!out) return IGKS_EINVAL;
+  *out = nullptr;
+  igks_ctx* ctx = new igks_ctx();
+  if (opt) ctx->opt = *opt;
+  if (ctx->opt.check_every <= 0) ctx->opt.check_every = 20;
+  if (ctx->opt.sweep_threads <= 0) ctx->opt.sweep_threads = 512;
+  if (ctx->opt.sweep_threads > 1024 || ctx->opt.sweep_threads % 32) { delete ctx; return IGKS_EINVAL; }
+  if (ctx->opt.precision != IGKS_PREC_FP64 && ctx->opt.precision != IGKS_PREC_MIXED) { delete ctx; return IGKS_EINVAL; }
+  cudaError_t e = cudaSetDevice(ctx->opt.device);
+  if (e != cudaSuccess) { delete ctx; return IGKS_ECUDA; }
+  if (ctx->opt.stream) {
+    ctx->stream = (cudaStream_t)ctx->opt.stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete ctx; return IGKS_ECUDA; }
+    ctx->own_stream = true;
+  }
+  if (ctx->opt.timing)
+    for (auto& ev : ctx->ev)
+      if (cudaEventCreate(&ev) != cudaSuccess) { igks_destroy(ctx); return IGKS_ECUDA; }
+  *out = ctx;
+  return IGKS_OK;
+}
+
+int igks_enqueue(igks_ctx* ctx, int32_t n_iters) {
+  if (!ctx || n_iters < 0) return IGKS_EINVAL;
+  int rc = build(ctx);
+  if (rc) return rc;
+  for (int r = 0; r < n_iters; r++) {
+    if (ctx->gexec) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+    else enqueue_iteration(ctx);
+  }
+  CK(cudaGetLastError());
+  return IGKS_OK;
+}
+
+int igks_kernel_times(igks_ctx* ctx, int32_t cap, float* ms, int32_t* n) {
+  if (!ctx || !ms || !n || cap < 0) return IGKS_EINVAL;
+  if (!ctx->opt.timing) return fail(ctx, IGKS_EBUSY, "context created without timing");
+  *n = LAUNCHES_PER_ITER;
+  for (int k = 0; k < LAUNCHES_PER_ITER && k < cap; k++) {
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, ctx->ev[k], ctx->ev[k + 1]));
+    ms[k] = t;
+  }
+  return IGKS_OK;
+}
+
+const char* igks_kernel_name(int32_t i) {
+  return (i >= 0 && i < LAUNCHES_PER_ITER) ? KERNEL_NAMES[i] : "";
+}
+
+int igks_mesh_upload(igks_ctx* ctx, int32_t n_nodes, const double* xy, int32_t n_cells,
+                     const int32_t* cell_ptr, const int32_t* cell_nodes, int32_t n_faces,
+                     const int32_t* face_nodes, const int32_t* face_cells, const int32_t* face_bc,
+                     int32_t* solve_id) {
+  if (!ctx) return IGKS_EINVAL;
+  if (ctx->built) return fail(ctx, IGKS_EBUSY, "mesh upload after the device data was built");
+  if (n_nodes <= 0 || n_cells <= 0 || n_faces <= 0 || !xy || !cell_ptr || !cell_nodes || !face_nodes ||
+      !face_cells || !face_bc)
+    return fail(ctx, IGKS_EINVAL, "null array or non-positive size");
+  HostMesh m;
+  m.nn = n_nodes; m.nc = n_cells; m.nf = n_faces;
+  if (cell_ptr[0] != 0) return fail(ctx, IGKS_EMESH, "cell_ptr[0] != 0");
+  for (int i = 0; i < n_cells; i++)
+    if (cell_ptr[i + 1] - cell_ptr[i] < 3) return fail(ctx, IGKS_EMESH, "cell with fewer than 3 nodes");
+  const int nk = cell_ptr[n_cells];
+  for (int k = 0; k < nk; k++)
+    if (cell_nodes[k] < 0 || cell_nodes[k] >= n_nodes) return fail(ctx, IGKS_EMESH, "cell node index out of range");
+  std::vector<int> deg(n_cells, 0);
+  for (int f = 0; f < n_faces; f++) {
+    int a = face_nodes[2 * f], b = face_nodes[2 * f + 1];
+    int l = face_cells[2 * f], r = face_cells[2 * f + 1];
+    if (a < 0 || a >= n_nodes || b < 0 || b >= n_nodes || a == b) return fail(ctx, IGKS_EMESH, "face node index out of range");
+    if (l < 0 || l >= n_cells) return fail(ctx, IGKS_EMESH, "face without a valid left cell");
+    if (r >= n_cells || r == l) return fail(ctx, IGKS_EMESH, "face right cell out of range");
+    if (r < 0 && (face_bc[f] < IGKS_BC_FARFIELD || face_bc[f] > IGKS_BC_WALL))
+      return fail(ctx, IGKS_EMESH, "boundary face without a boundary tag");
+    if (r >= 0 && face_bc[f] != IGKS_BC_INTERIOR) return fail(ctx, IGKS_EMESH, "interior face with a boundary tag");
+    deg[l]++;
+    if (r >= 0) deg[r]++;
+  }
+  for (int i = 0; i < n_cells; i++)
+    if (deg[i] != cell_ptr[i + 1] - cell_ptr[i]) return fail(ctx, IGKS_EMESH, "cell is not closed by its faces");
+  for (int k = 0; k < 2 * n_nodes; k++)
+    if (!std::isfinite(xy[k])) return fail(ctx, IGKS_EMESH, "non-finite node coordinate");
+  m.xy.assign(xy, xy + 2 * (size_t)n_nodes);
+  m.cell_ptr.assign(cell_ptr, cell_ptr + n_cells + 1);
+  m.cell_nodes.assign(cell_nodes, cell_nodes + nk);
+  m.face_nodes.assign(face_nodes, face_nodes + 2 * (size_t)n_faces);
+  m.face_cells.assign(face_cells, face_cells + 2 * (size_t)n_faces);
+  m.face_bc.assign(face_bc, face_bc + n_faces);
+  ctx->meshes.push_back(std::move(m));
+  ctx->flows.push_back(default_flow());
+  ctx->flow_set.push_back(0);
+  if (solve_id) *solve_id = (int32_t)ctx->meshes.size() - 1;
+  return IGKS_OK;
+}
+
+int igks_set_flow(igks_ctx* ctx, int32_t solve, const igks_flow* f) {
+  if (!ctx || !f || solve < 0 || solve >= (int)ctx->meshes.size()) return IGKS_EINVAL;
+  if (!(f->mach > 0) || !(f->reynolds > 0) || !(f->prandtl > 0) || !(f->cfl_exp > 0) || !(f->cfl_init > 0) ||
+      !(f->cfl_min > 0) || f->cfl_max < f->cfl_min || f->limiter < 0 || f->limiter > 2 || !(f->t_ref > 0))
+    return fail(ctx, IGKS_EINVAL, "invalid flow conditions");
+  ctx->flows[solve] = *f;
+  ctx->flow_set[solve] = 1;
+  if (ctx->built) {
+    DevFlow d = make_devflow(*f);
+    CK(h2d(ctx, (DevFlow*)ctx->dev.flow + solve, &d, sizeof d));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return IGKS_OK;
+}
+
+static int check_solve(igks_ctx* ctx, int32_t solve) {
+  if (!ctx || solve < 0 || solve >= (int)ctx->meshes.size()) return IGKS_EINVAL;
+  return 0;
+}
+
+int igks_init_freestream(igks_ctx* ctx, int32_t solve) {
+  if (check_solve(ctx, solve)) return IGKS_EINVAL;
+  int rc = build(ctx);
+  if (rc) return rc;
+  const HostMesh& m = ctx->meshes[solve];
+  DevFlow fl = make_devflow(ctx->flows[solve]);
+  std::vector<double> W((size_t)m.nc);
+  for (int v = 0; v < 5; v++) {
+    std::fill(W.begin(), W.end(), fl.Winf[v]);
+    CK(h2d(ctx, ctx->dev.W + (size_t)v * ctx->nc_pad + ctx->cell_off[solve], W.data(), sizeof(double) * m.nc));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  double sc[5] = {0.0, ctx->flows[solve].cfl_init, 0.0, 0.0, 0.0};
+  return igks_set_scalars(ctx, solve, sc);
+}
+
+int igks_iterate(igks_ctx* ctx, int32_t max_iters, igks_status* status) {
+  if (!ctx || max_iters < 0) return IGKS_EINVAL;
+  int rc = build(ctx);
+  if (rc) return rc;
+  CK(cudaSetDevice(ctx->opt.device));
+  const int ns = ctx->dev.n_solves;
+  int done = 0;
+  bool any_live = true;
+  while (done < max_iters && any_live) {
+    int k = std::min(ctx->opt.check_every, max_iters - done);
+    for (int r = 0; r < k; r++) {
+      if (ctx->gexec) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+      else enqueue_iteration(ctx);
+    }
+    CK(cudaGetLastError());
+    done += k;
+    CK(cudaMemcpyAsync(ctx->h_st, ctx->dev.st, sizeof(SolveState) * ns, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    any_live = false;
+    for (int s = 0; s < ns; s++) any_live |= (ctx->h_st[s].state == 0);
+  }
+  if (max_iters == 0) {
+    CK(cudaMemcpyAsync(ctx->h_st, ctx->dev.st, sizeof(SolveState) * ns, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  bool all_conv = true, any_div = false;
+  for (int s = 0; s < ns; s++) {
+    const SolveState& q = ctx->h_st[s];
+    if (status) {
+      igks_status& o = status[s];
+      o.iters = q.iter; o.state = q.state; o.res_l2_rho = q.res_l2;
+      o.res_l2_rel = q.res_l2_first > 0 ? q.res_l2 / q.res_l2_first : 0.0;
+      o.res_inf = q.res_inf; o.eq40_ratio = q.eq40; o.cfl = q.cfl; o.dt = q.dt;
+    }
+    all_conv &= (q.state == IGKS_CONVERGED);
+    any_div |= (q.state < 0);
+  }
+  if (any_div) return IGKS_DIVERGED;
+  return all_conv ? IGKS_CONVERGED : IGKS_OK;
+}
+
+// copy k components of a per-cell [k][nc_pad] array of a solve into out[k][n]
+static int get_cells(igks_ctx* ctx, int solve, const double* base, int k, double* out) {
+  const int n = ctx->meshes[solve].nc;
+  CK(d2h_2d(ctx, out, sizeof(double) * n, base + ctx->cell_off[solve], sizeof(double) * ctx->nc_pad,
+            sizeof(double) * n, k));
+  return 0;
+}
+
+static int get_faces(igks_ctx* ctx, int solve, const double* base, int k, double* out) {
+  const int n = ctx->meshes[solve].nf;
+  CK(d2h_2d(ctx, out, sizeof(double) * n, base + ctx->face_off[solve], sizeof(double) * ctx->nf,
+            sizeof(double) * n, k));
+  return 0;
+}
+
+int igks_get_fields(igks_ctx* ctx, int32_t solve, double* W) {
+  if (check_solve(ctx, solve) || !W) return IGKS_EINVAL;
+  int rc = build(ctx);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return get_cells(ctx, solve, ctx->dev.W, 5, W);
+}
+
+int igks_set_fields(igks_ctx* ctx, int32_t solve, const double* W) {
+  if (check_solve(ctx, solve) || !W) return IGKS_EINVAL;
+  int rc = build(ctx);
+  if (rc) return rc;
+  const int n = ctx->meshes[solve].nc;
+  for (int i = 0; i < n; i++)
+    if (!(W[i] > 0.0) || !std::isfinite(W[3 * (size_t)n + i])) return fail(ctx, IGKS_EINVAL, "non-physical state");
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(h2d_2d(ctx, ctx->dev.W + ctx->cell_off[solve], sizeof(double) * ctx->nc_pad, W, sizeof(double) * n,
+            sizeof(double) * n, 5));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return IGKS_OK;
+}
+
+int igks_get_scalars(igks_ctx* ctx, int32_t solve, double* out) {
+  if (check_solve(ctx, solve) || !out) return IGKS_EINVAL;
+  int rc = build(ctx);
+  if (rc) return rc;
+  SolveState q;
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(d2h(ctx, &q, ctx->dev.st + solve, sizeof q));
+  out[0] = q.iter; out[1] = q.cfl; out[2] = q.res_inf_prev; out[3] = q.res_l2_first; out[4] = q.state;
+  return IGKS_OK;
+}
+
+int igks_set_scalars(igks_ctx* ctx, int32_t solve, const double* in) {
+  if (check_solve(ctx, solve) || !in) return IGKS_EINVAL;
+  int rc = build(ctx);
+  if (rc) return rc;
+  SolveState q;
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(d2h(ctx, &q, ctx->dev.st + solve, sizeof q));
+  q.iter = (int)in[0]; q.cfl = in[1]; q.res_inf_prev = in[2]; q.res_l2_first = in[3]; q.state = (int)in[4];
+  q.pending = 0;
+  CK(h2d(ctx, ctx->dev.st + solve, &q, sizeof q));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return IGKS_OK;
+}
+
+int igks_get_array(igks_ctx* ctx, int32_t solve, int32_t which, double* out) {
+  if (check_solve(ctx, solve) || !out) return IGKS_EINVAL;
+  int rc = build(ctx);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  const Dev& d = ctx->dev;
+  const int n = ctx->meshes[solve].nc, nf = ctx->meshes[solve].nf;
+  switch (which) {
+    case IGKS_ARR_GRAD: return get_cells(ctx, solve, d.grad, 8, out);
+    case IGKS_ARR_PHI: return get_cells(ctx, solve, d.phi, 4, out);
+    case IGKS_ARR_LAMBDA_F: return get_faces(ctx, solve, d.lam_f, 1, out);
+    case IGKS_ARR_LAMBDA_C: return get_cells(ctx, solve, d.Lam, 1, out);
+    case IGKS_ARR_FLUX: return get_faces(ctx, solve, d.F, 6, out);
+    case IGKS_ARR_RES: return get_cells(ctx, solve, d.M, 5, out);
+    case IGKS_ARR_GHOST: {
+      rc = get_faces(ctx, solve, d.G, 5, out);
+      if (rc) return rc;
+      for (int f = 0; f < nf; f++)
+        if (ctx->meshes[solve].face_cells[2 * f + 1] >= 0)
+          for (int v = 0; v < 5; v++) out[(size_t)v * nf + f] = 0.0;
+      return 0;
+    }
+    case IGKS_ARR_DWSTAR:
+    case IGKS_ARR_DW: {
+      const void* src = which == IGKS_ARR_DWSTAR ? d.dWs : d.dW;
+      if (ctx->opt.precision == IGKS_PREC_MIXED) {
+        std::vector<float> tmp(5 * (size_t)n);
+        CK(d2h_2d(ctx, tmp.data(), sizeof(float) * n, (const float*)src + ctx->cell_off[solve],
+                  sizeof(float) * ctx->nc_pad, sizeof(float) * n, 5));
+        for (size_t k = 0; k < tmp.size(); k++) out[k] = tmp[k];
+        return 0;
+      }
+      return get_cells(ctx, solve, (const double*)src, 5, out);
+    }
+    case IGKS_ARR_GEOM_CELL:
+      if ((rc = get_cells(ctx, solve, d.area, 1, out))) return rc;
+      if ((rc = get_cells(ctx, solve, d.cx, 1, out + n))) return rc;
+      if ((rc = get_cells(ctx, solve, d.cy, 1, out + 2 * (size_t)n))) return rc;
+      return get_cells(ctx, solve, d.wall_d, 1, out + 3 * (size_t)n);
+    case IGKS_ARR_GEOM_FACE:
+      if ((rc = get_faces(ctx, solve, d.fS, 1, out))) return rc;
+      if ((rc = get_faces(ctx, solve, d.fnx, 1, out + nf))) return rc;
+      if ((rc = get_faces(ctx, solve, d.fny, 1, out + 2 * (size_t)nf))) return rc;
+      if ((rc = get_faces(ctx, solve, d.fmx, 1, out + 3 * (size_t)nf))) return rc;
+      return get_faces(ctx, solve, d.fmy, 1, out + 4 * (size_t)nf);
+  }
+  return fail(ctx, IGKS_EINVAL, "unknown array id");
+}
+
+int igks_mesh_info(igks_ctx* ctx, int32_t solve, int32_t* out) {
+  if (check_solve(ctx, solve) || !out) return IGKS_EINVAL;
+  int rc = build(ctx);
+  if (rc) return rc;
+  const HostMesh& m = ctx->meshes[solve];
+  out[0] = m.nc; out[1] = m.nf; out[2] = m.nlev_f; out[3] = m.nlev_b; out[4] = m.nbf;
+  return IGKS_OK;
+}
+
+int igks_get_forces(igks_ctx* ctx, int32_t solve, int32_t bc_tag, double* out) {
+  if (check_solve(ctx, solve) || !out) return IGKS_EINVAL;
+  int rc = build(ctx);
+  if (rc) return rc;
+  const HostMesh& m = ctx->meshes[solve];
+  std::vector<double> F(6 * (size_t)m.nf), G(5 * (size_t)m.nf), geo(5 * (size_t)m.nf);
+  SolveState q;
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(d2h(ctx, &q, ctx->dev.st + solve, sizeof q));
+  if ((rc = get_faces(ctx, solve, ctx->dev.F, 6, F.data()))) return rc;
+  if ((rc = get_faces(ctx, solve, ctx->dev.G, 5, G.data()))) return rc;
+  if ((rc = igks_get_array(ctx, solve, IGKS_ARR_GEOM_FACE, geo.data()))) return rc;
+  if (!(q.dt > 0.0)) return fail(ctx, IGKS_EBUSY, "no iteration has run yet");
+  double fx = 0, fy = 0, vx = 0, vy = 0;
+  const int nf = m.nf;
+  for (int f = 0; f < nf; f++) {
+    if (m.face_cells[2 * f + 1] >= 0 || m.face_bc[f] != bc_tag) continue;
+    // momentum through the face per unit time = force of the fluid on the boundary
+    double px = F[(size_t)nf + f] / q.dt, py = F[2 * (size_t)nf + f] / q.dt;
+    fx += px; fy += py;
+    double r = G[f], mx = G[(size_t)nf + f], my = G[2 * (size_t)nf + f], E = G[3 * (size_t)nf + f];
+    double p = (GAMMA - 1.0) * (E - 0.5 * (mx * mx + my * my) / r);
+    double S = geo[f], nx = geo[(size_t)nf + f], ny = geo[2 * (size_t)nf + f];
+    vx += px - p * nx * S;
+    vy += py - p * ny * S;
+  }
+  double a = ctx->flows[solve].aoa_deg * M_PI / 180.0;
+  double ca = std::cos(a), sa = std::sin(a);
+  out[0] = 2.0 * (-fx * sa + fy * ca);
+  out[1] = 2.0 * (fx * ca + fy * sa);
+  out[2] = 2.0 * (vx * ca + vy * sa);
+  return IGKS_OK;
+}
+
+int igks_launches_per_iteration(igks_ctx* ctx, int32_t* out) {
+  if (!ctx || !out) return IGKS_EINVAL;
+  *out = LAUNCHES_PER_ITER;
+  return IGKS_OK;
+}
+
+int igks_destroy(igks_ctx* ctx) {
+  if (!ctx) return IGKS_EINVAL;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  release(ctx);
+  for (auto& ev : ctx->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return IGKS_OK;
+}
+
+const char* igks_last_error(igks_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,606 @@
+// igks_kernels.cu -- per-cell and per-solve kernels of the IGKS iteration on sm_103a:
+// mesh geometry and wall distance (set-up), eddy viscosity, ghost cells (Section II.E),
+// least-squares gradients with limiter and spectral radius (Eq. 6-10, 20-23), residual
+// gather with the SA source (Eq. 16, 27-28a), residual norms and CFL adaptation (Eq. 25),
+// and the matrix-free LU-SGS sweeps (Eq. 19-22, 31-32) with the state update.
+//
+// The work is HBM/latency bound (no dense contraction): loads are structure-of-arrays,
+// per-cell reductions are done in registers, per-solve reductions in fixed order.
+#include <float.h>
+
+#include "igks_dev.h"
+#include "igks_phys.cuh"
+
+namespace igks {
+
+// ===================================================================================
+// set-up: geometry and wall distance
+// ===================================================================================
+
+__global__ void k_geometry_cells(Dev d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.nc_pad || d.cell_solve[i] < 0) return;
+  const double* X = d.xy;
+  const double* Y = d.xy + d.nn;
+  int b = d.cn_ptr[i], e = d.cn_ptr[i + 1];
+  double a = 0.0, sx = 0.0, sy = 0.0;
+  for (int k = b; k < e; k++) {
+    int p = d.cn_node[k], q = d.cn_node[k + 1 < e ? k + 1 : b];
+    double x0 = X[p], y0 = Y[p], x1 = X[q], y1 = Y[q];
+    double c = x0 * y1 - x1 * y0;
+    a += c;
+    sx += (x0 + x1) * c;
+    sy += (y0 + y1) * c;
+  }
+  a *= 0.5;
+  d.area[i] = a;
+  d.cx[i] = sx / (6.0 * a);
+  d.cy[i] = sy / (6.0 * a);
+  if (!(a > 0.0)) atomicOr(d.err + 0, 1);
+}
+
+__global__ void k_geometry_faces(Dev d) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= d.nf) return;
+  const double* X = d.xy;
+  const double* Y = d.xy + d.nn;
+  int a = d.fnode[f], b = d.fnode[d.nf + f];
+  double dx = X[b] - X[a], dy = Y[b] - Y[a];
+  double S = sqrt(dx * dx + dy * dy);
+  double nx = dy / S, ny = -dx / S;
+  double mx = 0.5 * (X[a] + X[b]), my = 0.5 * (Y[a] + Y[b]);
+  int L = d.fL[f], R = d.fR[f];
+  double cxl = d.cx[L], cyl = d.cy[L];
+  double dL = (mx - cxl) * nx + (my - cyl) * ny;
+  double cxr, cyr, dR;
+  if (R >= 0) {
+    cxr = d.cx[R]; cyr = d.cy[R];
+    dR = -((mx - cxr) * nx + (my - cyr) * ny);
+  } else {
+    cxr = cxl + 2.0 * dL * nx;
+    cyr = cyl + 2.0 * dL * ny;
+    dR = dL;
+  }
+  d.fS[f] = S; d.fnx[f] = nx; d.fny[f] = ny; d.fmx[f] = mx; d.fmy[f] = my;
+  d.fcx[f] = cxr; d.fcy[f] = cyr; d.fdL[f] = dL; d.fdR[f] = dR;
+  d.fdn[f] = fabs((cxr - cxl) * nx + (cyr - cyl) * ny);
+  if (!(dL > 0.0) || !(dR > 0.0) || !(S > 0.0)) atomicOr(d.err + 1, 1);
+}
+
+__global__ void k_wall_distance(Dev d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.nc_pad) return;
+  int s = d.cell_solve[i];
+  if (s < 0) return;
+  const double* X = d.xy;
+  const double* Y = d.xy + d.nn;
+  double px = d.cx[i], py = d.cy[i], dmin = 1e300;
+  for (int k = d.wall_ptr[s]; k < d.wall_ptr[s + 1]; k++) {
+    int f = d.wall_face[k];
+    int a = d.fnode[f], b = d.fnode[d.nf + f];
+    double ax = X[a], ay = Y[a], ex = X[b] - ax, ey = Y[b] - ay;
+    double t = ((px - ax) * ex + (py - ay) * ey) / (ex * ex + ey * ey);
+    t = fmin(fmax(t, 0.0), 1.0);
+    double qx = ax + t * ex - px, qy = ay + t * ey - py;
+    dmin = fmin(dmin, sqrt(qx * qx + qy * qy));
+  }
+  d.wall_d[i] = dmin;
+}
+
+void launch_geometry(const Dev& d, cudaStream_t s) {
+  k_geometry_cells<<<(d.nc_pad + 255) / 256, 256, 0, s>>>(d);
+  if (d.nf) k_geometry_faces<<<(d.nf + 255) / 256, 256, 0, s>>>(d);
+}
+
+void launch_wall_distance(const Dev& d, cudaStream_t s) {
+  k_wall_distance<<<(d.nc_pad + 255) / 256, 256, 0, s>>>(d);
+}
+
+// ===================================================================================
+// iteration kernels
+// ===================================================================================
+
+__device__ __forceinline__ bool cell_live(const Dev& d, int i, int* solve) {
+  if (i >= d.nc_pad) return false;
+  int s = d.cell_solve[i];
+  if (s < 0 || d.st[s].state != 0) return false;
+  *solve = s;
+  return true;
+}
+
+// laminar and eddy viscosity of every cell
+__global__ void __launch_bounds__(CELL_BLOCK) k_prep(Dev d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, s;
+  if (!cell_live(d, i, &s)) return;
+  const DevFlow& fl = d.flow[s];
+  int n = d.nc_pad;
+  double r = d.W[i], mx = d.W[n + i], my = d.W[2 * n + i], E = d.W[3 * n + i], nut = d.W[4 * n + i];
+  double mu = viscosity(fl, lambda_of(r, mx, my, E));
+  d.mu_l[i] = mu;
+  d.mu_t[i] = eddy_viscosity(fl, r, nut, mu);
+}
+
+// ghost states of the boundary faces
+__global__ void k_ghost(Dev d) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.nbf) return;
+  int f = d.bface[k];
+  int s = d.fsolve[f];
+  if (d.st[s].state != 0) return;
+  const DevFlow& fl = d.flow[s];
+  int i = d.fL[f], n = d.nc_pad;
+  double Wi[5], Wg[5];
+  for (int v = 0; v < 5; v++) Wi[v] = d.W[v * n + i];
+  ghost_state(fl, d.fbc[f], d.fnx[f], d.fny[f], Wi, Wg);
+  for (int v = 0; v < 5; v++) d.G[v * d.nf + f] = Wg[v];
+  double mu = viscosity(fl, lambda_of(Wg[0], Wg[1], Wg[2], Wg[3]));
+  d.Gmu[f] = mu;
+  d.Gmu[d.nf + f] = eddy_viscosity(fl, Wg[0], Wg[4], mu);
+}
+
+void launch_prep(const Dev& d, cudaStream_t s) {
+  k_prep<<<d.n_cell_blocks, CELL_BLOCK, 0, s>>>(d);
+}
+
+void launch_ghost(const Dev& d, cudaStream_t s) {
+  if (d.nbf) k_ghost<<<(d.nbf + 127) / 128, 128, 0, s>>>(d);
+}
+
+// state and viscosities of the cell across face f (ghost on a boundary)
+__device__ __forceinline__ void across_state(const Dev& d, int f, int j, double* Wk, double* mu, double* mut) {
+  if (j >= 0) {
+    int n = d.nc_pad;
+    for (int v = 0; v < 5; v++) Wk[v] = d.W[v * n + j];
+    *mu = d.mu_l[j]; *mut = d.mu_t[j];
+  } else {
+    for (int v = 0; v < 5; v++) Wk[v] = d.G[v * d.nf + f];
+    *mu = d.Gmu[f]; *mut = d.Gmu[d.nf + f];
+  }
+}
+
+// face spectral radius lambda_f = |Vbar.n| + cbar (+ viscous term), always evaluated with
+// the face's own left/right order so both cells get the same bits
+__device__ __forceinline__ double face_lambda(const DevFlow& fl, const double* WL, const double* WR,
+                                              double muL, double mtL, double muR, double mtR,
+                                              double nx, double ny, double dn) {
+  double pL = pressure_of(WL[0], WL[1], WL[2], WL[3]);
+  double pR = pressure_of(WR[0], WR[1], WR[2], WR[3]);
+  double uL = WL[1] / WL[0], vL = WL[2] / WL[0], cL = sqrt(GAMMA * pL / WL[0]);
+  double uR = WR[1] / WR[0], vR = WR[2] / WR[0], cR = sqrt(GAMMA * pR / WR[0]);
+  double ub = 0.5 * (uL + uR), vb = 0.5 * (vL + vR), cb = 0.5 * (cL + cR);
+  double lam = fabs(ub * nx + vb * ny) + cb;
+  if (fl.visc_sr) {
+    double mub = 0.5 * (muL + muR), mtb = 0.5 * (mtL + mtR), rb = 0.5 * (WL[0] + WR[0]);
+    lam += 2.0 * (mub + mtb) * GAMMA / (rb * fl.prandtl * dn);
+  }
+  return lam;
+}
+
+// Least-squares gradients (Eq. 7) of the conserved variables over the face neighbours
+// (ghosts included), the limiter of Eq. 9-10, the vorticity for SA, the face spectral
+// radius, Lambda_i and the per-solve minimum explicit time step (Eq. 23).
+__global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, s = -1;
+  bool live = cell_live(d, i, &s);
+  double dtc = DBL_MAX;
+  if (live) {
+    const DevFlow& fl = d.flow[s];
+    const int n = d.nc_pad;
+    double Wi[5];
+    for (int v = 0; v < 5; v++) Wi[v] = d.W[v * n + i];
+    double mui = d.mu_l[i], mti = d.mu_t[i];
+    double xi = d.cx[i], yi = d.cy[i];
+    double A00 = 0.0, A01 = 0.0, A11 = 0.0;
+    double r0[4] = {0, 0, 0, 0}, r1[4] = {0, 0, 0, 0}, wmax[4], wmin[4];
+    for (int v = 0; v < 4; v++) wmax[v] = wmin[v] = Wi[v];
+    double Lam = 0.0;
+    for (int k = d.cf_ptr[i]; k < d.cf_ptr[i + 1]; k++) {
+      int f = d.cf_face[k];
+      int L = d.fL[f], R = d.fR[f];
+      bool own = (L == i);
+      int j = own ? R : L;
+      double Wk[5], muk, mtk, xk, yk;
+      across_state(d, f, j, Wk, &muk, &mtk);
+      if (j >= 0) { xk = d.cx[j]; yk = d.cy[j]; } else { xk = d.fcx[f]; yk = d.fcy[f]; }
+      double dx = xk - xi, dy = yk - yi;
+      A00 += dx * dx; A01 += dx * dy; A11 += dy * dy;
+#pragma unroll
+      for (int v = 0; v < 4; v++) {
+        double dw = Wk[v] - Wi[v];
+        r0[v] += dx * dw;
+        r1[v] += dy * dw;
+        wmax[v] = fmax(wmax[v], Wk[v]);
+        wmin[v] = fmin(wmin[v], Wk[v]);
+      }
+      double lam = own ? face_lambda(fl, Wi, Wk, mui, mti, muk, mtk, d.fnx[f], d.fny[f], d.fdn[f])
+                       : face_lambda(fl, Wk, Wi, muk, mtk, mui, mti, d.fnx[f], d.fny[f], d.fdn[f]);
+      if (own) d.lam_f[f] = lam;
+      Lam += 0.5 * lam * d.fS[f];
+    }
+    double det = A00 * A11 - A01 * A01;
+    double area = d.area[i];
+    double b[8];
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      b[2 * v] = (A11 * r0[v] - A01 * r1[v]) / det;
+      b[2 * v + 1] = (A00 * r1[v] - A01 * r0[v]) / det;
+      d.grad[(2 * v) * n + i] = b[2 * v];
+      d.grad[(2 * v + 1) * n + i] = b[2 * v + 1];
+    }
+    double phi[4] = {1.0, 1.0, 1.0, 1.0};
+    if (fl.limiter != 0) {
+      double h = sqrt(area);
+      double eps2 = (fl.venkat_k * h) * (fl.venkat_k * h) * (fl.venkat_k * h);
+      for (int k = d.cn_ptr[i]; k < d.cn_ptr[i + 1]; k++) {
+        int nd = d.cn_node[k];
+        double ox = d.xy[nd] - xi, oy = d.xy[d.nn + nd] - yi;
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+          double dv = b[2 * v] * ox + b[2 * v + 1] * oy;
+          double pv = 1.0;
+          if (fl.limiter == 1) {
+            if (dv > 0.0) pv = fmin(1.0, (wmax[v] - Wi[v]) / dv);
+            else if (dv < 0.0) pv = fmin(1.0, (wmin[v] - Wi[v]) / dv);
+          } else if (dv != 0.0) {
+            double dp = dv > 0.0 ? wmax[v] - Wi[v] : wmin[v] - Wi[v];
+            pv = ((dp * dp + eps2) * dv + 2.0 * dv * dv * dp) / (dv * (dp * dp + 2.0 * dv * dv + dv * dp + eps2));
+          }
+          phi[v] = fmin(phi[v], pv);
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; v++) d.phi[v * n + i] = phi[v];
+    double u = Wi[1] / Wi[0], vv = Wi[2] / Wi[0];
+    double dudy = (b[3] - u * b[1]) / Wi[0];
+    double dvdx = (b[4] - vv * b[0]) / Wi[0];
+    d.omega[i] = fabs(dvdx - dudy);
+    d.Lam[i] = Lam;
+    dtc = fl.cfl_exp * area / Lam;
+  }
+  // block minimum -> one atomic per block; every block lies inside one solve
+  __shared__ double red[CELL_BLOCK / 32];
+  double m = dtc;
+  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < CELL_BLOCK / 32 ? red[threadIdx.x] : DBL_MAX;
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0 && m < DBL_MAX) {
+      int bs = d.cell_solve[blockIdx.x * CELL_BLOCK];
+      // positive doubles order like their bit patterns
+      if (bs >= 0) atomicMin(d.dt_bits + bs, (unsigned long long)__double_as_longlong(m));
+    }
+  }
+}
+
+void launch_gradient(const Dev& d, cudaStream_t s) {
+  k_gradient<<<d.n_cell_blocks, CELL_BLOCK, 0, s>>>(d);
+}
+
+// Residual M_i = -(1/dt) sum over the faces of cell i (ascending face order) of the signed
+// face flux (Eq. 16), the SA right-hand side Omega Sr + R (Eq. 27-28a), the SA diagonal
+// without its time term, and per-block partial norms of M_rho.
+__global__ void __launch_bounds__(CELL_BLOCK) k_residual(Dev d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, s = -1;
+  bool live = cell_live(d, i, &s);
+  double rmax = 0.0, r2 = 0.0;
+  if (live) {
+    const DevFlow& fl = d.flow[s];
+    const int n = d.nc_pad, nf = d.nf;
+    double dt = __longlong_as_double((long long)d.dt_bits[s]);
+    double acc[5] = {0, 0, 0, 0, 0}, sad = 0.0;
+    for (int k = d.cf_ptr[i]; k < d.cf_ptr[i + 1]; k++) {
+      int f = d.cf_face[k];
+      if (d.fL[f] == i) {
+#pragma unroll
+        for (int v = 0; v < 4; v++) acc[v] += d.F[v * nf + f];
+        acc[4] += d.F[4 * nf + f];
+        sad += d.sa_a[2 * nf + f];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 4; v++) acc[v] -= d.F[v * nf + f];
+        acc[4] += d.F[5 * nf + f];
+        sad += d.sa_a[3 * nf + f];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; v++) d.M[v * n + i] = -acc[v] / dt;
+    double area = d.area[i];
+    double m4 = 0.0, fw = 0.0, sdiag = 0.0;
+    if (fl.sa_on) {
+      const double k2 = SA_KAPPA * SA_KAPPA;
+      double r = d.W[i], nut = d.W[4 * n + i];
+      double nu = d.mu_l[i] / r;
+      double chi = nut / nu, c3 = chi * chi * chi;
+      double fv1 = c3 / (c3 + SA_CV1 * SA_CV1 * SA_CV1);
+      double fv2 = 1.0 - chi / (1.0 + chi * fv1);
+      double om = d.omega[i], dw = d.wall_d[i];
+      double Sbar = nut * fv2 / (k2 * dw * dw);
+      double St = (Sbar >= -SA_CV2 * om)
+                      ? om + Sbar
+                      : om + om * (SA_CV2 * SA_CV2 * om + SA_CV3 * Sbar) / ((SA_CV3 - 2.0 * SA_CV2) * om - Sbar);
+      double rr = (nut < 10.0 * St * k2 * dw * dw) ? nut / (St * k2 * dw * dw) : 10.0;
+      double r2_ = rr * rr, r6 = r2_ * r2_ * r2_;
+      double g = rr + SA_CW2 * (r6 - rr);
+      double g2 = g * g, g6 = g2 * g2 * g2;
+      const double c6 = SA_CW3 * SA_CW3 * SA_CW3 * SA_CW3 * SA_CW3 * SA_CW3;
+      fw = g * pow((1.0 + c6) / (g6 + c6), 1.0 / 6.0);
+      double Sr = SA_CB1 * St * nut - SA_CW1 * fw * (nut / dw) * (nut / dw);
+      m4 = area * Sr + acc[4];
+      sdiag = sad + area * 2.0 * SA_CW1 * fw * nut / (dw * dw);
+    }
+    d.M[4 * n + i] = m4;
+    d.fw[i] = fw;
+    d.sa_diag[i] = sdiag;
+    double mr = d.M[i];
+    rmax = fabs(mr);
+    double q = mr / area;
+    r2 = q * q;
+  }
+  __shared__ double smax[CELL_BLOCK / 32], ssum[CELL_BLOCK / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+  }
+  if ((threadIdx.x & 31) == 0) { smax[threadIdx.x >> 5] = rmax; ssum[threadIdx.x >> 5] = r2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < CELL_BLOCK / 32; w++) { a = fmax(a, smax[w]); b += ssum[w]; }
+    d.part[blockIdx.x] = a;
+    d.part[d.n_cell_blocks + blockIdx.x] = b;
+  }
+}
+
+void launch_residual(const Dev& d, cudaStream_t s) {
+  k_residual<<<d.n_cell_blocks, CELL_BLOCK, 0, s>>>(d);
+}
+
+// per-solve norms in fixed block order, CFL adaptation (Eq. 25), stopping rule
+__global__ void k_norms(Dev d) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.n_solves) return;
+  SolveState& st = d.st[s];
+  if (st.state != 0) return;
+  const DevFlow& fl = d.flow[s];
+  double rmax = 0.0, r2 = 0.0;
+  for (int b = st.blk_begin; b < st.blk_end; b++) {
+    rmax = fmax(rmax, d.part[b]);
+    r2 += d.part[d.n_cell_blocks + b];
+  }
+  st.dt = __longlong_as_double((long long)d.dt_bits[s]);
+  st.res_inf = rmax;
+  st.res_l2 = sqrt(r2 / (double)(st.cell_end - st.cell_begin));
+  if (st.iter == 0) {
+    st.cfl = fl.cfl_init;
+    st.res_l2_first = st.res_l2;
+  } else {
+    double c = st.cfl * st.res_inf_prev / st.res_inf;
+    st.cfl = fmin(fmax(c, fl.cfl_min), fl.cfl_max);
+  }
+  st.res_inf_prev = st.res_inf;
+  st.pending = (st.res_l2_first > 0.0 && st.res_l2 <= fl.res_target * st.res_l2_first) ? 1 : 0;
+}
+
+void launch_norms(const Dev& d, cudaStream_t s) {
+  k_norms<<<(d.n_solves + 63) / 64, 64, 0, s>>>(d);
+}
+
+__global__ void k_end_iter(Dev d) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.n_solves) return;
+  SolveState& st = d.st[s];
+  if (st.state != 0) return;
+  st.iter += 1;
+  st.state = st.pending;
+  d.dt_bits[s] = 0x7FF0000000000000ull;   // +inf: the next iteration's minimum starts here
+}
+
+void launch_end_iter(const Dev& d, cudaStream_t s) {
+  k_end_iter<<<(d.n_solves + 63) / 64, 64, 0, s>>>(d);
+}
+
+// ===================================================================================
+// LU-SGS sweeps (Eq. 19-22 mean flow, Eq. 31-32 SA), level-scheduled: one block per
+// solve walks its levels in order; cells of one level are independent. The increment
+// of the Euler flux of each processed cell, dF = F(W + dW) - F(W) in x and y, is formed
+// once by that cell in an incremental (difference-free) form and read by its
+// neighbours, which project it on their face normal.
+// ===================================================================================
+
+template <class T>
+__device__ __forceinline__ void delta_flux(T r, T mx, T my, T E, T dr, T dmx, T dmy, T dE, T* o) {
+  const T g1 = (T)(GAMMA - 1.0);
+  T r1 = r + dr;
+  T u = mx / r, v = my / r;
+  T inv = (T)1 / (r * r1);
+  T du = (dmx * r - mx * dr) * inv, dv = (dmy * r - my * dr) * inv;
+  T dmxu = dmx * u + mx * du + dmx * du;
+  T dmyv = dmy * v + my * dv + dmy * dv;
+  T p = g1 * (E - (T)0.5 * (mx * u + my * v));
+  T dp = g1 * (dE - (T)0.5 * (dmxu + dmyv));
+  T H = E + p, dH = dE + dp;
+  o[0] = dmx;                               // x: mass
+  o[1] = dmy;                               // y: mass
+  o[2] = dmxu + dp;                         // x: x-momentum
+  o[3] = dmx * v + mx * dv + dmx * dv;      // y: x-momentum
+  o[4] = dmy * u + my * du + dmy * du;      // x: y-momentum
+  o[5] = dmyv + dp;                         // y: y-momentum
+  o[6] = dH * u + H * du + dH * du;         // x: energy
+  o[7] = dH * v + H * dv + dH * dv;         // y: energy
+}
+
+template <class T>
+__global__ void k_sweep_fwd(Dev d) {
+  const int s = blockIdx.x;
+  const SolveState& st = d.st[s];
+  if (st.state != 0) return;
+  const DevFlow& fl = d.flow[s];
+  const int n = d.nc_pad, nf = d.nf;
+  const double cfl = st.cfl;
+  T* dWs = (T*)d.dWs;
+  T* dF = (T*)d.dF;
+  const int l0 = d.lvl_solve_ptr[s], l1 = d.lvl_solve_ptr[s + 1] - 1;
+  for (int l = l0; l < l1; l++) {
+    int b = d.fwd_lvl[l], e = d.fwd_lvl[l + 1];
+    for (int k = b + threadIdx.x; k < e; k += blockDim.x) {
+      int i = d.fwd_order[k];
+      T acc[5];
+#pragma unroll
+      for (int v = 0; v < 5; v++) acc[v] = (T)d.M[v * n + i];
+      for (int q = d.cf_ptr[i]; q < d.cf_ptr[i + 1]; q++) {
+        int f = d.cf_face[q];
+        int L = d.fL[f], R = d.fR[f];
+        if (R < 0) continue;                 // ghost increments are zero in this sweep
+        bool own = (L == i);
+        int j = own ? R : L;
+        if (j >= i) continue;
+        T sg = own ? (T)1 : (T)-1;
+        T nx = sg * (T)d.fnx[f], ny = sg * (T)d.fny[f];
+        T hS = (T)0.5 * (T)d.fS[f], lam = (T)d.lam_f[f];
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+          T dfn = dF[(2 * v) * n + j] * nx + dF[(2 * v + 1) * n + j] * ny;
+          acc[v] -= hS * (dfn - lam * dWs[v * n + j]);
+        }
+        if (fl.sa_on) acc[4] -= (T)d.sa_a[(own ? 0 : 1) * nf + f] * dWs[4 * n + j];
+      }
+      double Lam = d.Lam[i];
+      T D = (T)(Lam / cfl + Lam);
+      T dw[5];
+#pragma unroll
+      for (int v = 0; v < 4; v++) dw[v] = acc[v] / D;
+      dw[4] = fl.sa_on ? acc[4] / (T)(Lam / cfl + d.sa_diag[i]) : (T)0;
+#pragma unroll
+      for (int v = 0; v < 5; v++) dWs[v * n + i] = dw[v];
+      T o[8];
+      delta_flux<T>((T)d.W[i], (T)d.W[n + i], (T)d.W[2 * n + i], (T)d.W[3 * n + i], dw[0], dw[1], dw[2], dw[3], o);
+#pragma unroll
+      for (int c = 0; c < 8; c++) dF[c * n + i] = o[c];
+    }
+    __syncthreads();
+  }
+}
+
+template <class T>
+__global__ void k_sweep_bwd(Dev d) {
+  const int s = blockIdx.x;
+  SolveState& st = d.st[s];
+  if (st.state != 0) return;
+  const DevFlow& fl = d.flow[s];
+  const int n = d.nc_pad, nf = d.nf;
+  const double cfl = st.cfl;
+  T* dWs = (T*)d.dWs;
+  T* dWo = (T*)d.dW;
+  T* dF = (T*)d.dF;
+  double eq40 = 0.0;
+  int bad = 0;
+  const int l0 = d.blvl_solve_ptr[s], l1 = d.blvl_solve_ptr[s + 1] - 1;
+  for (int l = l0; l < l1; l++) {
+    int b = d.bwd_lvl[l], e = d.bwd_lvl[l + 1];
+    for (int k = b + threadIdx.x; k < e; k += blockDim.x) {
+      int i = d.bwd_order[k];
+      T ws[5];
+#pragma unroll
+      for (int v = 0; v < 5; v++) ws[v] = dWs[v * n + i];
+      T acc[5] = {0, 0, 0, 0, 0};
+      for (int q = d.cf_ptr[i]; q < d.cf_ptr[i + 1]; q++) {
+        int f = d.cf_face[q];
+        int L = d.fL[f], R = d.fR[f];
+        bool own = (L == i);
+        T sg = own ? (T)1 : (T)-1;
+        T nx = sg * (T)d.fnx[f], ny = sg * (T)d.fny[f];
+        T hS = (T)0.5 * (T)d.fS[f], lam = (T)d.lam_f[f];
+        if (R < 0) {
+          int bc = d.fbc[f];
+          if (bc == 1) continue;             // far-field increments are zero
+          // wall / symmetry ghost: boundary map of the cell's own forward increment
+          T g[5];
+          g[0] = ws[0]; g[3] = ws[3];
+          if (bc == 3) { g[1] = -ws[1]; g[2] = -ws[2]; g[4] = -ws[4]; }
+          else {
+            T fnx = (T)d.fnx[f], fny = (T)d.fny[f];
+            T mn = ws[1] * fnx + ws[2] * fny;
+            g[1] = ws[1] - (T)2 * mn * fnx; g[2] = ws[2] - (T)2 * mn * fny; g[4] = ws[4];
+          }
+          T o[8];
+          delta_flux<T>((T)d.G[f], (T)d.G[nf + f], (T)d.G[2 * nf + f], (T)d.G[3 * nf + f], g[0], g[1], g[2], g[3], o);
+#pragma unroll
+          for (int v = 0; v < 4; v++) acc[v] += hS * ((o[2 * v] * nx + o[2 * v + 1] * ny) - lam * g[v]);
+          if (fl.sa_on) acc[4] += (T)d.sa_a[f] * g[4];
+          continue;
+        }
+        int j = own ? R : L;
+        if (j <= i) continue;
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+          T dfn = dF[(2 * v) * n + j] * nx + dF[(2 * v + 1) * n + j] * ny;
+          acc[v] += hS * (dfn - lam * dWo[v * n + j]);
+        }
+        if (fl.sa_on) acc[4] += (T)d.sa_a[(own ? 0 : 1) * nf + f] * dWo[4 * n + j];
+      }
+      double Lam = d.Lam[i];
+      T D = (T)(Lam / cfl + Lam);
+      T dw[5];
+#pragma unroll
+      for (int v = 0; v < 4; v++) dw[v] = ws[v] - acc[v] / D;
+      dw[4] = fl.sa_on ? ws[4] - acc[4] / (T)(Lam / cfl + d.sa_diag[i]) : (T)0;
+#pragma unroll
+      for (int v = 0; v < 5; v++) dWo[v * n + i] = dw[v];
+      double Wi[5];
+#pragma unroll
+      for (int v = 0; v < 5; v++) Wi[v] = d.W[v * n + i];
+      T o[8];
+      delta_flux<T>((T)Wi[0], (T)Wi[1], (T)Wi[2], (T)Wi[3], dw[0], dw[1], dw[2], dw[3], o);
+#pragma unroll
+      for (int c = 0; c < 8; c++) dF[c * n + i] = o[c];
+      // update (FP64) and the Eq. 40 ratio
+      double num = 0.0, den = 0.0;
+#pragma unroll
+      for (int v = 0; v < 4; v++) {
+        double dv = (double)dw[v];
+        num += dv * dv;
+        den += Wi[v] * Wi[v];
+        Wi[v] += dv;
+      }
+      Wi[4] += (double)dw[4];
+      if (Wi[4] < 0.0) Wi[4] = 0.0;
+      eq40 = fmax(eq40, sqrt(num) / sqrt(den));
+      double p = pressure_of(Wi[0], Wi[1], Wi[2], Wi[3]);
+      if (!(Wi[0] > 0.0) || !(p > 0.0) || !isfinite(Wi[3]) || !isfinite(Wi[4])) bad = 1;
+#pragma unroll
+      for (int v = 0; v < 5; v++) d.W[v * n + i] = Wi[v];
+    }
+    __syncthreads();
+  }
+  // block reductions of the Eq. 40 ratio and the divergence flag
+  __shared__ double sm[32];
+  __shared__ int sb[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    eq40 = fmax(eq40, __shfl_xor_sync(0xffffffffu, eq40, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) { sm[threadIdx.x >> 5] = eq40; sb[threadIdx.x >> 5] = bad; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    int bb = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) { a = fmax(a, sm[w]); bb |= sb[w]; }
+    st.eq40 = a;
+    if (bb) st.pending = -5;
+  }
+}
+
+void launch_sweep_fwd(const Dev& d, int precision, int threads, cudaStream_t s) {
+  if (precision == 1) k_sweep_fwd<float><<<d.n_solves, threads, 0, s>>>(d);
+  else k_sweep_fwd<double><<<d.n_solves, threads, 0, s>>>(d);
+}
+
+void launch_sweep_bwd(const Dev& d, int precision, int threads, cudaStream_t s) {
+  if (precision == 1) k_sweep_bwd<float><<<d.n_solves, threads, 0, s>>>(d);
+  else k_sweep_bwd<double><<<d.n_solves, threads, 0, s>>>(d);
+}
+
+}  // namespace igks

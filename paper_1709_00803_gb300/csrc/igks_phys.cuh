@@ -1,0 +1,71 @@
+// igks_phys.cuh -- small device functions shared by the kernels of libigks: gas state,
+// viscosity, eddy viscosity and the ghost-cell boundary states of Section II.E.
+#pragma once
+#include "igks_dev.h"
+
+namespace igks {
+
+__device__ __forceinline__ double pressure_of(double r, double mx, double my, double E) {
+  return (GAMMA - 1.0) * (E - 0.5 * (mx * mx + my * my) / r);
+}
+
+// lambda = rho / (2 p) of Eq. 2
+__device__ __forceinline__ double lambda_of(double r, double mx, double my, double E) {
+  return r / (2.0 * pressure_of(r, mx, my, E));
+}
+
+// Sutherland's law relative to the free stream, T/T_inf = lambda_inf / lambda
+__device__ __forceinline__ double viscosity(const DevFlow& fl, double lam) {
+  double tr = fl.lam_inf / lam;
+  return fl.mu_inf * tr * sqrt(tr) * (1.0 + fl.s_star) / (tr + fl.s_star);
+}
+
+// eddy viscosity mu_t = rho nu_tilde fv1 (Eq. 34); zero for non-positive nu_tilde
+__device__ __forceinline__ double eddy_viscosity(const DevFlow& fl, double r, double nut, double mu) {
+  if (!fl.sa_on || !(nut > 0.0)) return 0.0;
+  double chi = nut * r / mu;
+  double c3 = chi * chi * chi;
+  return r * nut * c3 / (c3 + SA_CV1 * SA_CV1 * SA_CV1);
+}
+
+// ghost state of a boundary face from the interior centre state Wi (global frame)
+__device__ inline void ghost_state(const DevFlow& fl, int bc, double nx, double ny,
+                                   const double* Wi, double* Wg) {
+  if (bc == 3) {          // non-slip wall: momentum and nu_tilde reversed
+    Wg[0] = Wi[0]; Wg[1] = -Wi[1]; Wg[2] = -Wi[2]; Wg[3] = Wi[3]; Wg[4] = -Wi[4];
+    return;
+  }
+  if (bc == 2) {          // symmetry: normal momentum reversed
+    double mn = Wi[1] * nx + Wi[2] * ny;
+    Wg[0] = Wi[0]; Wg[1] = Wi[1] - 2.0 * mn * nx; Wg[2] = Wi[2] - 2.0 * mn * ny;
+    Wg[3] = Wi[3]; Wg[4] = Wi[4];
+    return;
+  }
+  // characteristic far field: Riemann invariants along the outward normal
+  const double g = GAMMA;
+  const double* Wf = fl.Winf;
+  double ri = Wi[0], ui = Wi[1] / ri, vi = Wi[2] / ri;
+  double pi = pressure_of(Wi[0], Wi[1], Wi[2], Wi[3]);
+  double ci = sqrt(g * pi / ri);
+  double ro = Wf[0], uo = Wf[1] / ro, vo = Wf[2] / ro;
+  double po = pressure_of(Wf[0], Wf[1], Wf[2], Wf[3]);
+  double co = sqrt(g * po / ro);
+  double uni = ui * nx + vi * ny, uno = uo * nx + vo * ny;
+  if (uni <= -ci) { for (int v = 0; v < 5; v++) Wg[v] = Wf[v]; return; }
+  if (uni >= ci) { for (int v = 0; v < 5; v++) Wg[v] = Wi[v]; return; }
+  double Rp = uni + 2.0 * ci / (g - 1.0);
+  double Rm = uno - 2.0 * co / (g - 1.0);
+  double ub = 0.5 * (Rp + Rm);
+  double cb = 0.25 * (g - 1.0) * (Rp - Rm);
+  double ut, vt, ent, nut;
+  if (ub > 0.0) { ut = ui - uni * nx; vt = vi - uni * ny; ent = pi / pow(ri, g); nut = Wi[4]; }
+  else          { ut = uo - uno * nx; vt = vo - uno * ny; ent = po / pow(ro, g); nut = Wf[4]; }
+  double rb = pow(cb * cb / (g * ent), 1.0 / (g - 1.0));
+  double pb = rb * cb * cb / g;
+  double ubx = ub * nx + ut, uby = ub * ny + vt;
+  Wg[0] = rb; Wg[1] = rb * ubx; Wg[2] = rb * uby;
+  Wg[3] = pb / (g - 1.0) + 0.5 * rb * (ubx * ubx + uby * uby);
+  Wg[4] = nut;
+}
+
+}  // namespace igks

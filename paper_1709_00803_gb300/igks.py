@@ -1,0 +1,223 @@
+"""Thin ctypes binding of libigks (include/igks.h). Argument marshalling only: every step
+of the IGKS iteration runs in the library's CUDA kernels. There is no CPU fallback: if the
+shared library cannot be built or loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, CONVERGED = 0, 1
+EINVAL, EMESH, ENOMEM, ECUDA, DIVERGED, TIMEOUT, EBUSY = -1, -2, -3, -4, -5, -6, -7
+PREC_FP64, PREC_MIXED = 0, 1
+ARR = dict(grad=1, phi=2, lambda_f=3, lambda_c=4, flux=5, res=6, dwstar=7, dw=8, ghost=9,
+           geom_cell=10, geom_face=11)
+
+
+class IgksError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libigks error {code}: {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
+                ("check_every", C.c_int32), ("use_graph", C.c_int32), ("sweep_threads", C.c_int32),
+                ("timing", C.c_int32), ("reserved", C.c_int32 * 6)]
+
+
+class Flow(C.Structure):
+    _fields_ = [("mach", C.c_double), ("reynolds", C.c_double), ("aoa_deg", C.c_double),
+                ("prandtl", C.c_double), ("t_ref", C.c_double), ("s_suth", C.c_double),
+                ("sa_on", C.c_int32), ("limiter", C.c_int32), ("nut_ratio_inf", C.c_double),
+                ("cfl_exp", C.c_double), ("cfl_init", C.c_double), ("cfl_min", C.c_double),
+                ("cfl_max", C.c_double), ("res_target", C.c_double), ("venkat_k", C.c_double),
+                ("c_num", C.c_double), ("visc_sr", C.c_int32), ("pad_", C.c_int32)]
+
+
+class Status(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("state", C.c_int32), ("res_l2_rho", C.c_double),
+                ("res_l2_rel", C.c_double), ("res_inf", C.c_double), ("eq40_ratio", C.c_double),
+                ("cfl", C.c_double), ("dt", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load (building first if needed) the in-tree libigks.so."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        P, i32, d = C.POINTER, C.c_int32, C.c_double
+        ip, dp, vp = P(C.c_int32), P(C.c_double), C.c_void_p
+        L.igks_create.argtypes = [P(Options), P(vp)]
+        L.igks_mesh_upload.argtypes = [vp, i32, dp, i32, ip, ip, i32, ip, ip, ip, ip]
+        L.igks_set_flow.argtypes = [vp, i32, P(Flow)]
+        L.igks_init_freestream.argtypes = [vp, i32]
+        L.igks_iterate.argtypes = [vp, i32, P(Status)]
+        L.igks_get_fields.argtypes = [vp, i32, dp]
+        L.igks_set_fields.argtypes = [vp, i32, dp]
+        L.igks_get_scalars.argtypes = [vp, i32, dp]
+        L.igks_set_scalars.argtypes = [vp, i32, dp]
+        L.igks_get_array.argtypes = [vp, i32, i32, dp]
+        L.igks_mesh_info.argtypes = [vp, i32, ip]
+        L.igks_get_forces.argtypes = [vp, i32, i32, dp]
+        L.igks_launches_per_iteration.argtypes = [vp, ip]
+        L.igks_destroy.argtypes = [vp]
+        L.igks_last_error.argtypes = [vp]
+        L.igks_last_error.restype = C.c_char_p
+        L.igks_enqueue.argtypes = [vp, i32]
+        L.igks_kernel_times.argtypes = [vp, i32, P(C.c_float), ip]
+        L.igks_kernel_name.argtypes = [i32]
+        L.igks_kernel_name.restype = C.c_char_p
+        for name in ("igks_create", "igks_mesh_upload", "igks_set_flow", "igks_init_freestream",
+                     "igks_iterate", "igks_get_fields", "igks_set_fields", "igks_get_scalars",
+                     "igks_set_scalars", "igks_get_array", "igks_mesh_info", "igks_get_forces",
+                     "igks_launches_per_iteration", "igks_destroy", "igks_enqueue", "igks_kernel_times"):
+            getattr(L, name).restype = C.c_int32
+        _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def to_flow(flow) -> Flow:
+    d = flow.as_dict() if hasattr(flow, "as_dict") else dict(flow)
+    f = Flow()
+    for name, _ in Flow._fields_:
+        if name in d:
+            setattr(f, name, d[name])
+    return f
+
+
+class Context:
+    """One igks_ctx: a set of steady solves resident on one GPU."""
+
+    def __init__(self, precision=PREC_FP64, device=0, stream=None, check_every=20, use_graph=1,
+                 sweep_threads=0, timing=0):
+        o = Options(precision=precision, device=device, stream=stream, check_every=check_every,
+                    use_graph=use_graph, sweep_threads=sweep_threads, timing=timing)
+        h = C.c_void_p()
+        rc = lib().igks_create(C.byref(o), C.byref(h))
+        if rc:
+            raise IgksError(rc, "igks_create failed")
+        self.h = h
+        self.meshes = []
+        self.precision = precision
+
+    def _check(self, rc, ok=(OK,)):
+        if rc not in ok:
+            raise IgksError(rc, lib().igks_last_error(self.h).decode())
+        return rc
+
+    # --- C ABI, same names ---
+    def mesh_upload(self, mesh) -> int:
+        xy = np.ascontiguousarray(mesh.xy, dtype=np.float64).ravel()
+        cp = np.ascontiguousarray(mesh.cell_ptr, dtype=np.int32)
+        cn = np.ascontiguousarray(mesh.cell_nodes, dtype=np.int32)
+        fn = np.ascontiguousarray(mesh.face_nodes, dtype=np.int32).ravel()
+        fc = np.ascontiguousarray(mesh.face_cells, dtype=np.int32).ravel()
+        fb = np.ascontiguousarray(mesh.face_bc, dtype=np.int32)
+        sid = C.c_int32()
+        self._check(lib().igks_mesh_upload(self.h, mesh.n_nodes, _dp(xy), mesh.n_cells, _ip(cp), _ip(cn),
+                                           mesh.n_faces, _ip(fn), _ip(fc), _ip(fb), C.byref(sid)))
+        self.meshes.append(mesh)
+        return sid.value
+
+    def set_flow(self, solve, flow):
+        f = to_flow(flow)
+        self._check(lib().igks_set_flow(self.h, solve, C.byref(f)))
+
+    def init_freestream(self, solve):
+        self._check(lib().igks_init_freestream(self.h, solve))
+
+    def iterate(self, max_iters):
+        st = (Status * len(self.meshes))()
+        rc = self._check(lib().igks_iterate(self.h, max_iters, st), ok=(OK, CONVERGED, DIVERGED))
+        return rc, [s.as_dict() for s in st]
+
+    def enqueue(self, n_iters):
+        self._check(lib().igks_enqueue(self.h, n_iters))
+
+    def kernel_times(self):
+        ms = (C.c_float * 32)()
+        n = C.c_int32()
+        self._check(lib().igks_kernel_times(self.h, 32, ms, C.byref(n)))
+        return {lib().igks_kernel_name(k).decode(): float(ms[k]) for k in range(n.value)}
+
+    def get_fields(self, solve, out=None):
+        shape = (5, self.meshes[solve].n_cells)
+        W = np.zeros(shape) if out is None else out
+        assert W.shape == shape and W.dtype == np.float64 and W.flags.c_contiguous
+        self._check(lib().igks_get_fields(self.h, solve, _dp(W)))
+        return W
+
+    def set_fields(self, solve, W):
+        if not (isinstance(W, np.ndarray) and W.dtype == np.float64 and W.flags.c_contiguous):
+            W = np.ascontiguousarray(W, dtype=np.float64)
+        assert W.shape == (5, self.meshes[solve].n_cells)
+        self._check(lib().igks_set_fields(self.h, solve, _dp(W)))
+
+    def get_scalars(self, solve):
+        o = np.zeros(5)
+        self._check(lib().igks_get_scalars(self.h, solve, _dp(o)))
+        return dict(iter=int(o[0]), cfl=o[1], res_inf_prev=o[2], res_l2_first=o[3], state=int(o[4]))
+
+    def set_scalars(self, solve, sc):
+        o = np.array([sc["iter"], sc["cfl"], sc["res_inf_prev"], sc["res_l2_first"], sc["state"]], dtype=np.float64)
+        self._check(lib().igks_set_scalars(self.h, solve, _dp(o)))
+
+    def get_array(self, solve, which):
+        m = self.meshes[solve]
+        n, nf = m.n_cells, m.n_faces
+        shapes = dict(grad=(4, 2, n), phi=(4, n), lambda_f=(nf,), lambda_c=(n,), flux=(6, nf), res=(5, n),
+                      dwstar=(5, n), dw=(5, n), ghost=(5, nf), geom_cell=(4, n), geom_face=(5, nf))
+        out = np.zeros(shapes[which])
+        self._check(lib().igks_get_array(self.h, solve, ARR[which], _dp(out)))
+        return out
+
+    def mesh_info(self, solve):
+        o = np.zeros(5, dtype=np.int32)
+        self._check(lib().igks_mesh_info(self.h, solve, _ip(o)))
+        return dict(n_cells=int(o[0]), n_faces=int(o[1]), levels_fwd=int(o[2]), levels_bwd=int(o[3]),
+                    n_boundary=int(o[4]))
+
+    def get_forces(self, solve, bc_tag=3):
+        o = np.zeros(3)
+        self._check(lib().igks_get_forces(self.h, solve, bc_tag, _dp(o)))
+        return dict(cl=o[0], cd=o[1], cd_viscous=o[2])
+
+    def launches_per_iteration(self):
+        o = C.c_int32()
+        self._check(lib().igks_launches_per_iteration(self.h, C.byref(o)))
+        return o.value
+
+    def destroy(self):
+        if getattr(self, "h", None):
+            lib().igks_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -1,0 +1,59 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/igks.h
+declares; the binding's structures match the header's layout. No GPU needed."""
+import ctypes as C
+import re
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "igks.h")).read()
+    return re.findall(r"^(?:int|const char\*)\s+(igks_\w+)\(", src, re.M)
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1709_00803_gb300 import igks
+    L = igks.lib()
+    names = _declared()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """sizeof and field offsets as the C compiler lays them out, against ctypes."""
+    from paper_1709_00803_gb300 import igks
+    checks = {"igks_flow": igks.Flow, "igks_status": igks.Status, "igks_options": igks.Options}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "igks.h"', "int main(void){"]
+    for cname, py in checks.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)]).decode().split("\n")
+    for line in filter(None, out):
+        cname, field, val = line.split()
+        py = checks[cname]
+        if field == "size":
+            assert C.sizeof(py) == int(val), line
+        else:
+            assert getattr(py, field).offset == int(val), line
+
+
+def test_oracle_and_library_share_no_code():
+    """Neither side includes, imports or links the other."""
+    csrc = os.path.join(ROOT, "paper_1709_00803_gb300", "csrc")
+    for f in os.listdir(csrc):
+        txt = open(os.path.join(csrc, f)).read()
+        assert "oracle" not in txt.lower(), f
+    for f in ("igks_oracle.c", "igks_oracle.h", "__init__.py"):
+        txt = open(os.path.join(ROOT, "oracle", f)).read()
+        assert "paper_1709_00803_gb300" not in txt and "igks_dev" not in txt and "igks.h" not in txt, f
