@@ -16,6 +16,8 @@ LIB = os.path.join(OUT_DIR, "libigks.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
+# per translation unit: the cell kernels round every product before adding (see igks_cell.cu)
+PER_FILE = {"igks_cell.cu": ["-fmad=false"]}
 _lock = threading.Lock()
 
 
@@ -47,7 +49,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         objs, procs = [], []
         for src in sources():
             obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-            cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+            cmd = [nvcc(), *ARCH, *FLAGS, *PER_FILE.get(os.path.basename(src), []), *extra, "-c", src, "-o", obj]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             procs.append((subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT), src))

@@ -159,16 +159,16 @@ static void enqueue_iteration(igks_ctx* ctx) {
   const int p = ctx->opt.precision, th = ctx->opt.sweep_threads;
   const bool t = ctx->opt.timing != 0;
   int e = 0;
-  if (t) cudaEventRecord(ctx->ev[e++], s);
-  launch_prep(d, s);                   if (t) cudaEventRecord(ctx->ev[e++], s);
-  launch_ghost(d, s);                  if (t) cudaEventRecord(ctx->ev[e++], s);
-  launch_gradient(d, s);               if (t) cudaEventRecord(ctx->ev[e++], s);
-  launch_flux(d, s);                   if (t) cudaEventRecord(ctx->ev[e++], s);
-  launch_residual(d, s);               if (t) cudaEventRecord(ctx->ev[e++], s);
-  launch_norms(d, s);                  if (t) cudaEventRecord(ctx->ev[e++], s);
-  launch_sweep_fwd(d, p, th, s);       if (t) cudaEventRecord(ctx->ev[e++], s);
-  launch_sweep_bwd(d, p, th, s);       if (t) cudaEventRecord(ctx->ev[e++], s);
-  launch_end_iter(d, s);               if (t) cudaEventRecord(ctx->ev[e++], s);
+  if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
+  launch_prep(d, s);                   if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
+  launch_ghost(d, s);                  if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
+  launch_gradient(d, s);               if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
+  launch_flux(d, s);                   if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
+  launch_residual(d, s);               if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
+  launch_norms(d, s);                  if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
+  launch_sweep_fwd(d, p, th, s);       if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
+  launch_sweep_bwd(d, p, th, s);       if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
+  launch_end_iter(d, s);               if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
 }
 
 // dependency levels of the sequential sweep: forward uses lower neighbours, backward upper
@@ -456,6 +456,19 @@ int igks_mesh_upload(igks_ctx* ctx, int32_t n_nodes, const double* xy, int32_t n
   }
   for (int i = 0; i < n_cells; i++)
     if (deg[i] != cell_ptr[i + 1] - cell_ptr[i]) return fail(ctx, IGKS_EMESH, "cell is not closed by its faces");
+  // every face is an edge of its cells: a -> b in the left cell's node cycle, b -> a in the right's
+  auto has_edge = [&](int c, int a, int b) {
+    const int s0 = cell_ptr[c], n = cell_ptr[c + 1] - s0;
+    for (int k = 0; k < n; k++)
+      if (cell_nodes[s0 + k] == a && cell_nodes[s0 + (k + 1) % n] == b) return true;
+    return false;
+  };
+  for (int f = 0; f < n_faces; f++) {
+    int a = face_nodes[2 * f], b = face_nodes[2 * f + 1];
+    int l = face_cells[2 * f], r = face_cells[2 * f + 1];
+    if (!has_edge(l, a, b)) return fail(ctx, IGKS_EMESH, "face is not an edge of its left cell (a->b)");
+    if (r >= 0 && !has_edge(r, b, a)) return fail(ctx, IGKS_EMESH, "face is not an edge of its right cell (b->a)");
+  }
   for (int k = 0; k < 2 * n_nodes; k++)
     if (!std::isfinite(xy[k])) return fail(ctx, IGKS_EMESH, "non-finite node coordinate");
   m.xy.assign(xy, xy + 2 * (size_t)n_nodes);
