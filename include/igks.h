@@ -199,6 +199,31 @@ int igks_launches_per_iteration(igks_ctx* ctx, int32_t* out);
 /* Release all device memory and the context. */
 int igks_destroy(igks_ctx* ctx);
 
+/* Residual norms of one solve without any allocation by the library (the paper has no
+ * counterpart: this is a service for callers that cannot let a library allocate GPU
+ * memory -- code running while the stream is being captured into a CUDA graph, hosts
+ * whose GPU memory comes only from their own pool or arena, real-time loops that cannot
+ * afford an allocation's latency or failure).
+ *   m_rho  DEVICE pointer, [n_cells] density residual M_rho of Eq. 16, one per cell
+ *   area   DEVICE pointer, [n_cells] cell areas Omega
+ *   out    DEVICE pointer, [2]: out[0] = max |M_rho| (the norm of Eq. 25),
+ *                               out[1] = RMS over cells of M_rho / Omega
+ *   stream cudaStream_t the two kernels run on (NULL: the legacy default stream)
+ * It computes the same reduction, in the same order, as igks_iterate does for its
+ * status. Inputs and outputs belong to the caller; the only other memory used is a
+ * fixed scratch array in the library's device data (IGKS_NOALLOC_MAX_CELLS / 256 * 2
+ * doubles = 64 KiB, held on every GPU that loads the library until the process exits).
+ * Its device address is looked up once per device, with that device current, by the
+ * first call made on that device: make that first call before any stream capture.
+ * Every call shares the scratch array and it keeps the last call's contents; each call
+ * writes all it reads, but calls whose kernels overlap on the GPU race on it.
+ * Asynchronous: returns after enqueueing; out is valid once the stream reaches it.
+ * Errors: IGKS_EINVAL for null pointers, n_cells <= 0 or n_cells > IGKS_NOALLOC_MAX_CELLS
+ * (message in igks_last_error(NULL)), IGKS_ECUDA for a CUDA error. */
+#define IGKS_NOALLOC_MAX_CELLS (1 << 20)
+int igks_residual_norms_noalloc(const double* m_rho, const double* area, int32_t n_cells,
+                                double* out, void* stream);
+
 /* Message of the last error on this context (owned by the context; never NULL). */
 const char* igks_last_error(igks_ctx* ctx);
 

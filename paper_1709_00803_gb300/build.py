@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
 # per translation unit: the cell kernels round every product before adding (see igks_cell.cu)
-PER_FILE = {"igks_cell.cu": ["-fmad=false"]}
+PER_FILE = {"igks_cell.cu": ["-fmad=false"], "igks_noalloc.cu": ["-fmad=false"]}
 _lock = threading.Lock()
 
 

@@ -18,6 +18,9 @@
 
 using namespace igks;
 
+// last error of the context-free entry point (igks_noalloc.cu)
+const char* igks_noalloc_last_error_();
+
 namespace {
 
 struct HostMesh {
@@ -733,7 +736,7 @@ int igks_destroy(igks_ctx* ctx) {
 }
 
 const char* igks_last_error(igks_ctx* ctx) {
-  if (!ctx) return "null context";
+  if (!ctx) return igks_noalloc_last_error_();
   return ctx->err.c_str();
 }
 

@@ -79,6 +79,8 @@ def lib():
         L.igks_kernel_times.argtypes = [vp, i32, P(C.c_float), ip]
         L.igks_kernel_name.argtypes = [i32]
         L.igks_kernel_name.restype = C.c_char_p
+        L.igks_residual_norms_noalloc.argtypes = [vp, vp, i32, vp, vp]
+        L.igks_residual_norms_noalloc.restype = C.c_int32
         for name in ("igks_create", "igks_mesh_upload", "igks_set_flow", "igks_init_freestream",
                      "igks_iterate", "igks_get_fields", "igks_set_fields", "igks_get_scalars",
                      "igks_set_scalars", "igks_get_array", "igks_mesh_info", "igks_get_forces",
@@ -90,6 +92,20 @@ def lib():
 
 def library_path() -> str:
     return _build.LIB
+
+
+NOALLOC_MAX_CELLS = 1 << 20
+
+
+def residual_norms_noalloc(m_rho_ptr: int, area_ptr: int, n_cells: int, out_ptr: int, stream: int = 0) -> int:
+    """igks_residual_norms_noalloc: DEVICE pointers in and out (e.g. tensor.data_ptr());
+    the library allocates nothing for it. Returns the status code; raises on error."""
+    L = lib()
+    rc = L.igks_residual_norms_noalloc(C.c_void_p(m_rho_ptr), C.c_void_p(area_ptr), n_cells,
+                                       C.c_void_p(out_ptr), C.c_void_p(stream))
+    if rc != OK:
+        raise IgksError(rc, L.igks_last_error(None).decode())
+    return rc
 
 
 def _dp(a):
