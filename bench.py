@@ -169,12 +169,19 @@ def main():
     ap.add_argument("--impl", default="igks", choices=["igks", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default="turbulent_plate", choices=list(WORKLOADS))
+    ap.add_argument("--ordering", default="as_given", choices=["as_given", "multicolor"],
+                    help="cell numbering = LU-SGS sweep order (the oracle baseline runs the same)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     mk, fl_fn, desc = WORKLOADS[args.workload]
     mesh, flow = mk(), fl_fn()
+    if args.ordering == "multicolor":
+        from paper_1709_00803_gb300 import igks as _ig
+        perm, ncol = _ig.order_cells(mesh, _ig.ORDER_MULTICOLOR)
+        mesh = mesh.renumbered(perm)
+        desc += f", multicolour cell order ({ncol} colours)"
     if args.impl == "reference":
         return run_reference(args, mesh, flow, desc)
 
@@ -268,7 +275,8 @@ def main():
            "data": "synthetic",
            "config": {"workload": desc, "cells": mesh.n_cells, "faces": mesh.n_faces,
                       "sweep_levels": [info["levels_fwd"], info["levels_bwd"]],
-                      "precision": args.precision, "parallelism": "replicas" if ws > 1 else "single solve",
+                      "precision": args.precision, "ordering": args.ordering,
+                      "parallelism": "replicas" if ws > 1 else "single solve",
                       "l2": "flushed between steps (256 MiB write outside the timed intervals)"},
            "e2e": e2e, "gpu_launches": ctx.launches_per_iteration() * args.steps,
            "kernel_ms": {k: round(v, 5) for k, v in kmean.items()},

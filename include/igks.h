@@ -65,7 +65,9 @@ typedef struct igks_options {
   int32_t use_graph;      /* capture one iteration as a CUDA graph and replay it */
   int32_t sweep_threads;  /* threads per block of the sweep kernels (0: default) */
   int32_t timing;         /* record CUDA events around every kernel (igks_kernel_times) */
-  int32_t reserved[6];
+  int32_t sweep_mode;     /* 0 automatic, 1 one block per solve walking its levels,
+                             2 one launch per level over all solves (low-depth orderings) */
+  int32_t reserved[5];
 } igks_options;
 
 /* Flow conditions of one solve. Non-dimensional: free-stream density, speed and the
@@ -195,6 +197,18 @@ int igks_get_forces(igks_ctx* ctx, int32_t solve, int32_t bc_tag, double* out /*
 
 /* Number of kernel launches one iteration issues (for launch accounting). */
 int igks_launches_per_iteration(igks_ctx* ctx, int32_t* out);
+
+/* Cell numbering for the LU-SGS sweeps (host only, no context). The sweep order of
+ * Eq. 20 is the cell numbering, so a renumbering changes the method's iterates (and its
+ * convergence rate), not its steady answer; apply the permutation to the mesh before
+ * upload (and to any reference run) to use it.
+ *   mode 0: identity (the mesh's own numbering)
+ *   mode 1: greedy multicolouring of the face-adjacency graph in index order, cells then
+ *           sorted by (colour, index): every sweep level is one colour
+ * perm[k] = old index of the cell placed at position k; *n_colors receives the number
+ * of colours (mode 1) or 1 (mode 0). Errors: IGKS_EINVAL, IGKS_EMESH. */
+int igks_order_cells(int32_t n_cells, int32_t n_faces, const int32_t* face_cells /*[2*n_faces]*/,
+                     int32_t mode, int32_t* perm /*[n_cells]*/, int32_t* n_colors);
 
 /* Release all device memory and the context. */
 int igks_destroy(igks_ctx* ctx);

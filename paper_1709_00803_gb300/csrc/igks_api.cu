@@ -54,7 +54,8 @@ struct igks_ctx {
   std::vector<int> cell_off, cell_pad, face_off, node_off;
   SolveState* h_st = nullptr;   // pinned mirror of the per-solve state
   int nc_pad = 0, nf = 0, nn = 0;
-  cudaEvent_t ev[LAUNCHES_PER_ITER + 1] = {};
+  cudaEvent_t ev[N_KERNEL_KINDS + 1] = {};
+  std::vector<int> h_wfwd_ptr, h_wbwd_ptr;   // wide schedule level offsets (host copies)
 };
 
 static int fail(igks_ctx* c, int code, const std::string& msg) {
@@ -150,9 +151,9 @@ static void release(igks_ctx* ctx) {
   ctx->built = false;
 }
 
-static const char* const KERNEL_NAMES[LAUNCHES_PER_ITER] = {
+static const char* const KERNEL_NAMES[N_KERNEL_KINDS] = {
     "k_prep", "k_ghost", "k_gradient", "k_flux", "k_residual", "k_norms",
-    "k_sweep_fwd", "k_sweep_bwd", "k_end_iter"};
+    "k_sweep_prep", "k_sweep_fwd", "k_sweep_bwd", "k_update", "k_end_iter"};
 
 // issue one iteration's kernels on the context stream (with an event after each kernel
 // when timing is on; event k+1 minus event k is the duration of kernel k)
@@ -169,8 +170,10 @@ static void enqueue_iteration(igks_ctx* ctx) {
   launch_flux(d, s);                   if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
   launch_residual(d, s);               if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
   launch_norms(d, s);                  if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
+  launch_sweep_prep(d, p, s);          if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
   launch_sweep_fwd(d, p, th, s);       if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
   launch_sweep_bwd(d, p, th, s);       if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
+  launch_update(d, p, s);              if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
   launch_end_iter(d, s);               if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
 }
 
@@ -227,6 +230,7 @@ static int build(igks_ctx* ctx) {
   std::vector<double> xy(2 * (size_t)nn);
   std::vector<int> fL(nf), fR(nf), fbc(nf), fsolve(nf), fnode(2 * (size_t)nf), bface, wall_face, wall_ptr(ns + 1, 0);
   std::vector<int> fwd_order, fwd_lvl, bwd_order, bwd_lvl, lsp(ns + 1, 0), blsp(ns + 1, 0);
+  std::vector<int> fs_ptr(1, 0), fs_j, fs_slot, cf_to_fs, bs_ptr(1, 0), bs_j, bs_slot, cf_to_bs;
   std::vector<SolveState> st(ns);
   std::vector<DevFlow> dfl(ns);
   for (int s = 0; s < ns; s++) {
@@ -288,6 +292,48 @@ static int build(igks_ctx* ctx) {
     for (int c : ord) bwd_order.push_back(co + c);
     for (int p : lvl) bwd_lvl.push_back(base + p);
     blsp[s + 1] = (int)bwd_lvl.size();
+    // narrow-schedule stencils in sweep-position order, with shared-memory ring slots: a
+    // neighbour produced at position q is still in the ring while the current level (end
+    // e) is processed iff q >= e - RING (no position written during the level maps to its
+    // slot)
+    cf_to_fs.resize(cf_face.size(), -1);
+    cf_to_bs.resize(cf_face.size(), -1);
+    for (int dir = 0; dir < 2; dir++) {
+      const bool fwd = dir == 0;
+      std::vector<int> ordl, lvll;
+      sweep_levels(m, lp, lf, fwd, ordl, lvll);
+      std::vector<int> pos(m.nc);
+      for (int p = 0; p < m.nc; p++) pos[ordl[p]] = p;
+      std::vector<int>& sptr = fwd ? fs_ptr : bs_ptr;
+      std::vector<int>& sj = fwd ? fs_j : bs_j;
+      std::vector<int>& sslot = fwd ? fs_slot : bs_slot;
+      std::vector<int>& map = fwd ? cf_to_fs : cf_to_bs;
+      for (int l = 0; l + 1 < (int)lvll.size(); l++) {
+        const int e = lvll[l + 1];
+        for (int p = lvll[l]; p < e; p++) {
+          const int i = ordl[p];
+          for (int k = lp[i]; k < lp[i + 1]; k++) {
+            const int f = lf[k];
+            const int l_ = m.face_cells[2 * f], r_ = m.face_cells[2 * f + 1];
+            const int kg = cf_ptr[co + i] + (k - lp[i]);
+            if (r_ < 0) {
+              if (!fwd && (m.face_bc[f] == IGKS_BC_WALL || m.face_bc[f] == IGKS_BC_SYMMETRY)) {
+                map[kg] = (int)sj.size();
+                sj.push_back(-1 - (fo + f));
+                sslot.push_back(-1);
+              }
+              continue;
+            }
+            const int j = (l_ == i) ? r_ : l_;
+            if (fwd ? (j >= i) : (j <= i)) continue;
+            map[kg] = (int)sj.size();
+            sj.push_back(co + j);
+            sslot.push_back(pos[j] >= e - RING ? pos[j] % RING : -1);
+          }
+          sptr.push_back((int)sj.size());
+        }
+      }
+    }
     // state
     SolveState& q = st[s];
     std::memset(&q, 0, sizeof q);
@@ -297,6 +343,38 @@ static int build(igks_ctx* ctx) {
     q.cell_begin = co;
     q.cell_end = co + m.nc;
     dfl[s] = make_devflow(ctx->flows[s]);
+  }
+  // ---- narrow schedule: per-position padded stencils (PF_E entries) and positions ----
+  const int P = (int)fwd_order.size();
+  std::vector<int> pos_f(nc, -1), pos_b(nc, -1), pb_of_pf(P), cnt_f(P), cnt_b(P);
+  std::vector<int> ej_f((size_t)PF_E * P, 0), eslot_f((size_t)PF_E * P, -1);
+  std::vector<int> ej_b((size_t)PF_E * P, 0), eslot_b((size_t)PF_E * P, -1);
+  std::vector<int> cf_to_ef(cf_face.size(), -1), cf_to_eb(cf_face.size(), -1);
+  for (int p = 0; p < P; p++) { pos_f[fwd_order[p]] = p; pos_b[bwd_order[p]] = p; }
+  for (int p = 0; p < P; p++) pb_of_pf[p] = pos_b[fwd_order[p]];
+  for (int dir = 0; dir < 2; dir++) {
+    const bool fwd = dir == 0;
+    const std::vector<int>& sptr = fwd ? fs_ptr : bs_ptr;
+    const std::vector<int>& sj = fwd ? fs_j : bs_j;
+    const std::vector<int>& sslot = fwd ? fs_slot : bs_slot;
+    const std::vector<int>& map = fwd ? cf_to_fs : cf_to_bs;
+    std::vector<int>& cnt = fwd ? cnt_f : cnt_b;
+    std::vector<int>& ej = fwd ? ej_f : ej_b;
+    std::vector<int>& es = fwd ? eslot_f : eslot_b;
+    std::vector<int>& emap = fwd ? cf_to_ef : cf_to_eb;
+    std::vector<int> inv(sj.size(), -1);
+    for (size_t k = 0; k < map.size(); k++)
+      if (map[k] >= 0) inv[map[k]] = (int)k;
+    for (int p = 0; p < P; p++) {
+      const int q0 = sptr[p], m_ = sptr[p + 1] - q0;
+      if (m_ > PF_E) { cnt[p] = -1; continue; }
+      cnt[p] = m_;
+      for (int e = 0; e < m_; e++) {
+        ej[(size_t)e * P + p] = sj[q0 + e];
+        es[(size_t)e * P + p] = sslot[q0 + e];
+        emap[inv[q0 + e]] = e * P + p;
+      }
+    }
   }
   // ---- device buffers ----
   Dev& d = ctx->dev;
@@ -323,6 +401,51 @@ static int build(igks_ctx* ctx) {
   AL(G, double, 5 * (size_t)nf); AL(Gmu, double, 2 * (size_t)nf);
   AL(st, SolveState, ns); AL(dt_bits, unsigned long long, ns);
   AL(part, double, 2 * (size_t)d.n_cell_blocks); AL(err, int, 4);
+  AL(eq40_bits, unsigned long long, ns); AL(bad, int, ns);
+  d.nnz = (int)cf_face.size();
+  AL(sw_cell, double, 5 * (size_t)nc); AL(sw_st, double, 4 * (size_t)d.nnz); AL(sw_j, int, d.nnz);
+  UP(fs_ptr, fs_ptr); UP(fs_j, fs_j); UP(fs_slot, fs_slot); UP(cf_to_fs, cf_to_fs);
+  UP(bs_ptr, bs_ptr); UP(bs_j, bs_j); UP(bs_slot, bs_slot); UP(cf_to_bs, cf_to_bs);
+  d.nfs = (int)fs_j.size();
+  d.nbs = (int)bs_j.size();
+  AL(sc_f, double, 4 * (size_t)std::max(d.nfs, 1)); AL(sc_b, double, 4 * (size_t)std::max(d.nbs, 1));
+  d.npos = P;
+  UP(pos_f, pos_f); UP(pos_b, pos_b); UP(pb_of_pf, pb_of_pf); UP(cnt_f, cnt_f); UP(cnt_b, cnt_b);
+  UP(ej_f, ej_f); UP(eslot_f, eslot_f); UP(ej_b, ej_b); UP(eslot_b, eslot_b);
+  UP(cf_to_ef, cf_to_ef); UP(cf_to_eb, cf_to_eb);
+  AL(rec_f, double, 13 * (size_t)P); AL(rec_b, double, 15 * (size_t)P);
+  AL(ec_f, double, 4 * (size_t)PF_E * P); AL(ec_b, double, 4 * (size_t)PF_E * P);
+  setup_sweeps();
+  {
+    // wide schedule: level l of every solve, solves in order
+    int maxf = 0, maxb = 0;
+    for (int s = 0; s < ns; s++) {
+      maxf = std::max(maxf, lsp[s + 1] - lsp[s] - 1);
+      maxb = std::max(maxb, blsp[s + 1] - blsp[s] - 1);
+    }
+    int mode = ctx->opt.sweep_mode;
+    d.wide = (mode == 2) || (mode == 0 && std::max(maxf, maxb) <= WIDE_MAX_LEVELS);
+    std::vector<int> wf, wb;
+    ctx->h_wfwd_ptr.assign(1, 0);
+    ctx->h_wbwd_ptr.assign(1, 0);
+    for (int l = 0; l < maxf; l++) {
+      for (int s = 0; s < ns; s++)
+        if (l < lsp[s + 1] - lsp[s] - 1)
+          for (int k = fwd_lvl[lsp[s] + l]; k < fwd_lvl[lsp[s] + l + 1]; k++) wf.push_back(fwd_order[k]);
+      ctx->h_wfwd_ptr.push_back((int)wf.size());
+    }
+    for (int l = 0; l < maxb; l++) {
+      for (int s = 0; s < ns; s++)
+        if (l < blsp[s + 1] - blsp[s] - 1)
+          for (int k = bwd_lvl[blsp[s] + l]; k < bwd_lvl[blsp[s] + l + 1]; k++) wb.push_back(bwd_order[k]);
+      ctx->h_wbwd_ptr.push_back((int)wb.size());
+    }
+    UP(wfwd_cells, wf); UP(wbwd_cells, wb);
+    d.h_wfwd_ptr = ctx->h_wfwd_ptr.data();
+    d.h_wbwd_ptr = ctx->h_wbwd_ptr.data();
+    d.n_wfwd = maxf;
+    d.n_wbwd = maxb;
+  }
 #undef UP
 #undef AL
   CK(h2d(ctx, d.st, st.data(), sizeof(SolveState) * ns));
@@ -380,8 +503,8 @@ int igks_create(const igks_options* opt, igks_ctx** out) {
   igks_ctx* ctx = new igks_ctx();
   if (opt) ctx->opt = *opt;
   if (ctx->opt.check_every <= 0) ctx->opt.check_every = 20;
-  if (ctx->opt.sweep_threads <= 0) ctx->opt.sweep_threads = 512;
-  if (ctx->opt.sweep_threads > 1024 || ctx->opt.sweep_threads % 32) { delete ctx; return IGKS_EINVAL; }
+  if (ctx->opt.sweep_threads <= 0) ctx->opt.sweep_threads = NARROW_THREADS;
+  if (ctx->opt.sweep_threads > NARROW_THREADS || ctx->opt.sweep_threads % 32) { delete ctx; return IGKS_EINVAL; }
   if (ctx->opt.precision != IGKS_PREC_FP64 && ctx->opt.precision != IGKS_PREC_MIXED) { delete ctx; return IGKS_EINVAL; }
   cudaError_t e = cudaSetDevice(ctx->opt.device);
   if (e != cudaSuccess) { delete ctx; return IGKS_ECUDA; }
@@ -414,8 +537,8 @@ int igks_enqueue(igks_ctx* ctx, int32_t n_iters) {
 int igks_kernel_times(igks_ctx* ctx, int32_t cap, float* ms, int32_t* n) {
   if (!ctx || !ms || !n || cap < 0) return IGKS_EINVAL;
   if (!ctx->opt.timing) return fail(ctx, IGKS_EBUSY, "context created without timing");
-  *n = LAUNCHES_PER_ITER;
-  for (int k = 0; k < LAUNCHES_PER_ITER && k < cap; k++) {
+  *n = N_KERNEL_KINDS;
+  for (int k = 0; k < N_KERNEL_KINDS && k < cap; k++) {
     float t = 0.0f;
     CK(cudaEventElapsedTime(&t, ctx->ev[k], ctx->ev[k + 1]));
     ms[k] = t;
@@ -424,7 +547,7 @@ int igks_kernel_times(igks_ctx* ctx, int32_t cap, float* ms, int32_t* n) {
 }
 
 const char* igks_kernel_name(int32_t i) {
-  return (i >= 0 && i < LAUNCHES_PER_ITER) ? KERNEL_NAMES[i] : "";
+  return (i >= 0 && i < N_KERNEL_KINDS) ? KERNEL_NAMES[i] : "";
 }
 
 int igks_mesh_upload(igks_ctx* ctx, int32_t n_nodes, const double* xy, int32_t n_cells,
@@ -718,9 +841,56 @@ int igks_get_forces(igks_ctx* ctx, int32_t solve, int32_t bc_tag, double* out) {
   return IGKS_OK;
 }
 
+int igks_order_cells(int32_t n_cells, int32_t n_faces, const int32_t* face_cells, int32_t mode, int32_t* perm,
+                     int32_t* n_colors) {
+  if (n_cells <= 0 || n_faces < 0 || !face_cells || !perm || (mode != 0 && mode != 1)) return IGKS_EINVAL;
+  if (mode == 0) {
+    for (int i = 0; i < n_cells; i++) perm[i] = i;
+    if (n_colors) *n_colors = 1;
+    return IGKS_OK;
+  }
+  // adjacency through interior faces
+  std::vector<int> ptr(n_cells + 1, 0), adj;
+  for (int f = 0; f < n_faces; f++) {
+    int l = face_cells[2 * f], r = face_cells[2 * f + 1];
+    if (l < 0 || l >= n_cells || r >= n_cells) return IGKS_EMESH;
+    if (r >= 0) { ptr[l + 1]++; ptr[r + 1]++; }
+  }
+  for (int i = 0; i < n_cells; i++) ptr[i + 1] += ptr[i];
+  adj.assign(ptr[n_cells], 0);
+  {
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    for (int f = 0; f < n_faces; f++) {
+      int l = face_cells[2 * f], r = face_cells[2 * f + 1];
+      if (r >= 0) { adj[fill[l]++] = r; adj[fill[r]++] = l; }
+    }
+  }
+  // greedy colouring in index order: smallest colour not used by a coloured neighbour
+  std::vector<int> col(n_cells, -1), mark;
+  int nc = 0;
+  for (int i = 0; i < n_cells; i++) {
+    mark.assign(nc + 1, 0);
+    for (int k = ptr[i]; k < ptr[i + 1]; k++)
+      if (col[adj[k]] >= 0) mark[col[adj[k]]] = 1;
+    int c = 0;
+    while (c < nc && mark[c]) c++;
+    col[i] = c;
+    nc = std::max(nc, c + 1);
+  }
+  // stable order by colour
+  std::vector<int> cnt(nc + 1, 0);
+  for (int i = 0; i < n_cells; i++) cnt[col[i] + 1]++;
+  for (int c = 0; c < nc; c++) cnt[c + 1] += cnt[c];
+  for (int i = 0; i < n_cells; i++) perm[cnt[col[i]]++] = i;
+  if (n_colors) *n_colors = nc;
+  return IGKS_OK;
+}
+
 int igks_launches_per_iteration(igks_ctx* ctx, int32_t* out) {
   if (!ctx || !out) return IGKS_EINVAL;
-  *out = LAUNCHES_PER_ITER;
+  int rc = build(ctx);
+  if (rc) return rc;
+  *out = N_KERNEL_KINDS - 2 + (ctx->dev.wide ? ctx->dev.n_wfwd + ctx->dev.n_wbwd : 2);
   return IGKS_OK;
 }
 

@@ -399,9 +399,13 @@ __global__ void k_end_iter(Dev d) {
   if (s >= d.n_solves) return;
   SolveState& st = d.st[s];
   if (st.state != 0) return;
+  st.eq40 = __longlong_as_double((long long)d.eq40_bits[s]);
+  if (d.bad[s]) st.pending = -5;   // IGKS_DIVERGED
   st.iter += 1;
   st.state = st.pending;
   d.dt_bits[s] = 0x7FF0000000000000ull;   // +inf: the next iteration's minimum starts here
+  d.eq40_bits[s] = 0ull;
+  d.bad[s] = 0;
 }
 
 void launch_end_iter(const Dev& d, cudaStream_t s) {

@@ -85,10 +85,41 @@ struct Dev {
   const int* bwd_order; const int* bwd_lvl;
   const int* lvl_solve_ptr;                     // [n_solves+1] into fwd_lvl (levels per solve)
   const int* blvl_solve_ptr;                    // [n_solves+1] into bwd_lvl
+  // sweep pre-pass results (type T of the sweep precision)
+  void* sw_cell;                 // [5][nc_pad]: 1/D, 1/a_ii (SA), u, v, E + p
+  void* sw_st;                   // [4][nnz]: signed hS nx, hS ny, hS lambda, SA coefficient
+  int* sw_j;                     // [nnz] neighbour across each cell-face entry, -1 on a boundary
+  int nnz;                       // entries of the cell -> face CSR
+  // narrow schedule: stencils in sweep-position order (positions index fwd_order /
+  // bwd_order). Forward entries are the lower neighbours, backward entries the upper
+  // neighbours plus wall/symmetry ghosts (j = -1 - face). slot >= 0: the neighbour's
+  // increments are still in the block's shared-memory ring at that slot.
+  const int* fs_ptr; const int* fs_j; const int* fs_slot; const int* cf_to_fs;
+  const int* bs_ptr; const int* bs_j; const int* bs_slot; const int* cf_to_bs;
+  void* sc_f; void* sc_b;        // [4][entries] coefficients (T), written by the pre-pass
+  int nfs, nbs;                  // entry counts
+  // narrow schedule, per sweep position p (P = npos = all real cells): records of
+  // per-iteration data in position-major SoA, and up to PF_E stencil entries padded per
+  // position (cnt < 0: more entries than that, use the CSR stencil above)
+  int npos;
+  const int* pos_f; const int* pos_b;            // [nc_pad] position of a cell (-1 padding)
+  void* rec_f;                                   // [13][P] T: M[5], r, mx, my, 1/D, 1/a_ii, u, v, H
+  void* rec_b;                                   // [15][P] T: W[5], 1/D, 1/a_ii, u, v, H, dW*[5]
+  void* ec_f; void* ec_b;                        // [4][PF_E][P] T: sx, sy, s lambda, SA coefficient
+  const int* cnt_f; const int* ej_f; const int* eslot_f; const int* pb_of_pf;
+  const int* cnt_b; const int* ej_b; const int* eslot_b;
+  const int* cf_to_ef; const int* cf_to_eb;      // [nnz] e * P + p, or -1
+  // wide schedule: cells of each level of all solves
+  int wide;                      // 1: one launch per level; 0: one block per solve
+  const int* wfwd_cells; const int* wbwd_cells;
+  const int* h_wfwd_ptr; const int* h_wbwd_ptr;   // HOST arrays of level offsets (launch sizes)
+  int n_wfwd, n_wbwd;
   // per solve
   const DevFlow* flow;
   SolveState* st;
   unsigned long long* dt_bits;   // [n_solves] atomic min of the explicit time step
+  unsigned long long* eq40_bits; // [n_solves] atomic max of the Eq. 40 ratio
+  int* bad;                      // [n_solves] divergence flag of the current update
   double* part;                  // [2][n_blocks] residual norm partials per cell block
   int n_cell_blocks;
   int* err;                      // [4] device error flags (mesh orientation, area)
@@ -104,9 +135,16 @@ void launch_gradient(const Dev& d, cudaStream_t s);
 void launch_flux(const Dev& d, cudaStream_t s);
 void launch_residual(const Dev& d, cudaStream_t s);
 void launch_norms(const Dev& d, cudaStream_t s);
+void setup_sweeps();   // kernel attributes (shared-memory ring size), once per build
+void launch_sweep_prep(const Dev& d, int precision, cudaStream_t s);
 void launch_sweep_fwd(const Dev& d, int precision, int threads, cudaStream_t s);
 void launch_sweep_bwd(const Dev& d, int precision, int threads, cudaStream_t s);
+void launch_update(const Dev& d, int precision, cudaStream_t s);
 void launch_end_iter(const Dev& d, cudaStream_t s);
-constexpr int LAUNCHES_PER_ITER = 9;
+constexpr int N_KERNEL_KINDS = 11;   // kernels of one iteration (the wide sweeps launch per level)
+constexpr int RING = 1024;           // shared-memory ring of the narrow sweeps (cells)
+constexpr int PF_E = 4;              // stencil entries held per prefetched sweep position
+constexpr int NARROW_THREADS = 256;  // block of the narrow sweeps (one thread per cell of a level)
+constexpr int WIDE_MAX_LEVELS = 64;  // automatic choice: wide schedule up to this many levels
 
 }  // namespace igks

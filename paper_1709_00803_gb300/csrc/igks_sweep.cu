@@ -1,5 +1,23 @@
 // igks_sweep.cu -- matrix-free LU-SGS forward and backward sweeps (Eq. 19-22 for the
 // mean flow, Eq. 31-32 for the SA variable) with the FP64 state update, in FP64 or FP32.
+//
+// Each sweep visits the cells in the dependency order of the sequential sweep of Eq. 20
+// (cell i needs its lower neighbours j < i forward, its upper neighbours j > i backward),
+// grouped into levels of mutually independent cells. Everything that does not depend on
+// the unknowns is formed first by a parallel pre-pass (1/D, velocities, enthalpy, the
+// signed face coefficients of every cell's stencil), so the dependency chain carries only
+// the neighbour contributions, one multiply by 1/D and the incremental flux of the new
+// increment. On GB300 each warp-wide FP64 instruction costs the same whatever the number
+// of active lanes, so the chain's FP64 instruction count sets the time of a level.
+//
+// Two schedules:
+//  - narrow: one block per solve walks its levels with a block barrier between them (for
+//    orderings with hundreds of thin levels). The increments of the last RING cells it
+//    produced stay in a shared-memory ring, so a cell usually reads its neighbours'
+//    increments from shared memory; its stencil (neighbour, ring slot, coefficients) is
+//    stored in sweep-position order so it is fetched without an indirection;
+//  - wide: one launch per level covering that level's cells of every solve (for low-depth
+//    orderings, e.g. multicolour, whose few levels hold thousands of cells each).
 #include <float.h>
 
 #include "igks_dev.h"
@@ -7,180 +25,232 @@
 
 namespace igks {
 
-// ===================================================================================
-// LU-SGS sweeps (Eq. 19-22 mean flow, Eq. 31-32 SA), level-scheduled: one block per
-// solve walks its levels in order; cells of one level are independent. The increment
-// of the Euler flux of each processed cell, dF = F(W + dW) - F(W) in x and y, is formed
-// once by that cell in an incremental (difference-free) form and read by its
-// neighbours, which project it on their face normal.
-// ===================================================================================
-
+// Increment of the x and y Euler fluxes for the increment (dr, dmx, dmy, dE) of a state
+// with density r, momenta mx, my, velocity u, v and total enthalpy density H = E + p,
+// written without differences of large numbers. o = {x mass, y mass, x x-mom, y x-mom,
+// x y-mom, y y-mom, x energy, y energy}.
 template <class T>
-__device__ __forceinline__ void delta_flux(T r, T mx, T my, T E, T dr, T dmx, T dmy, T dE, T* o) {
+__device__ __forceinline__ void delta_flux(T r, T mx, T my, T u, T v, T H, T dr, T dmx, T dmy, T dE, T* o) {
   const T g1 = (T)(GAMMA - 1.0);
-  T r1 = r + dr;
-  T u = mx / r, v = my / r;
-  T inv = (T)1 / (r * r1);
-  T du = (dmx * r - mx * dr) * inv, dv = (dmy * r - my * dr) * inv;
-  T dmxu = dmx * u + mx * du + dmx * du;
-  T dmyv = dmy * v + my * dv + dmy * dv;
-  T p = g1 * (E - (T)0.5 * (mx * u + my * v));
-  T dp = g1 * (dE - (T)0.5 * (dmxu + dmyv));
-  T H = E + p, dH = dE + dp;
-  o[0] = dmx;                               // x: mass
-  o[1] = dmy;                               // y: mass
-  o[2] = dmxu + dp;                         // x: x-momentum
-  o[3] = dmx * v + mx * dv + dmx * dv;      // y: x-momentum
-  o[4] = dmy * u + my * du + dmy * du;      // x: y-momentum
-  o[5] = dmyv + dp;                         // y: y-momentum
-  o[6] = dH * u + H * du + dH * du;         // x: energy
-  o[7] = dH * v + H * dv + dH * dv;         // y: energy
+  const T inv1 = (T)1 / (r + dr);
+  const T du = (dmx - u * dr) * inv1, dv = (dmy - v * dr) * inv1;
+  const T u1 = u + du, v1 = v + dv;
+  const T dmxu = dmx * u1 + mx * du;      // increment of mx u
+  const T dmyv = dmy * v1 + my * dv;      // increment of my v
+  const T dp = g1 * (dE - (T)0.5 * (dmxu + dmyv));
+  const T dH = dE + dp;
+  o[0] = dmx;
+  o[1] = dmy;
+  o[2] = dmxu + dp;
+  o[3] = dmx * v1 + mx * dv;
+  o[4] = dmy * u1 + my * du;
+  o[5] = dmyv + dp;
+  o[6] = dH * u1 + H * du;
+  o[7] = dH * v1 + H * dv;
+}
+
+// Contribution of one stencil entry to a cell's sweep sum: (1/2) S (dF . n - lambda dW)
+// for the mean flow (sx, sy = signed S n / 2, sl = S lambda / 2) and a_ij dnu for SA,
+// subtracted from (forward) or added to (backward) the cell's accumulator. Every schedule
+// applies the entries of a cell with these helpers in the same order, so a solve gives
+// the same bits whichever schedule runs it (alone or in a batch).
+template <class T>
+__device__ __forceinline__ void fwd_acc(T* acc, T sx, T sy, T sl, T sa, const T* f, const T* w, bool sa_on) {
+#pragma unroll
+  for (int v = 0; v < 4; v++) acc[v] -= sx * f[2 * v] + sy * f[2 * v + 1] - sl * w[v];
+  if (sa_on) acc[4] -= sa * w[4];
 }
 
 template <class T>
-__global__ void k_sweep_fwd(Dev d) {
-  const int s = blockIdx.x;
-  const SolveState& st = d.st[s];
-  if (st.state != 0) return;
+__device__ __forceinline__ void bwd_acc(T* acc, T sx, T sy, T sl, T sa, const T* f, const T* w, bool sa_on) {
+#pragma unroll
+  for (int v = 0; v < 4; v++) acc[v] += sx * f[2 * v] + sy * f[2 * v + 1] - sl * w[v];
+  if (sa_on) acc[4] += sa * w[4];
+}
+
+// ---- pre-pass: per-cell constants and the signed stencil of every cell ----
+template <class T>
+__global__ void __launch_bounds__(CELL_BLOCK) k_sweep_prep(Dev d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.nc_pad) return;
+  const int s = d.cell_solve[i];
+  if (s < 0 || d.st[s].state != 0) return;
   const DevFlow& fl = d.flow[s];
   const int n = d.nc_pad, nf = d.nf;
-  const double cfl = st.cfl;
-  T* dWs = (T*)d.dWs;
-  T* dF = (T*)d.dF;
-  const int l0 = d.lvl_solve_ptr[s], l1 = d.lvl_solve_ptr[s + 1] - 1;
-  for (int l = l0; l < l1; l++) {
-    int b = d.fwd_lvl[l], e = d.fwd_lvl[l + 1];
-    for (int k = b + threadIdx.x; k < e; k += blockDim.x) {
-      int i = d.fwd_order[k];
-      T acc[5];
+  const double cfl = d.st[s].cfl;
+  const double Lam = d.Lam[i];
+  const double r = d.W[i], mx = d.W[n + i], my = d.W[2 * n + i], E = d.W[3 * n + i];
+  const double u = mx / r, v = my / r;
+  const double p = (GAMMA - 1.0) * (E - 0.5 * (mx * u + my * v));
+  T* c = (T*)d.sw_cell;
+  c[i] = (T)(1.0 / (Lam / cfl + Lam));                                  // 1/D (Eq. 20, 24)
+  c[n + i] = fl.sa_on ? (T)(1.0 / (Lam / cfl + d.sa_diag[i])) : (T)0;   // 1/a_ii (Eq. 32)
+  c[2 * n + i] = (T)u;
+  c[3 * n + i] = (T)v;
+  c[4 * n + i] = (T)(E + p);
+  // position-ordered records of the narrow schedule
+  {
+    const int P = d.npos, pf = d.pos_f[i], pb = d.pos_b[i];
+    T* rf = (T*)d.rec_f;
+    T* rb = (T*)d.rec_b;
 #pragma unroll
-      for (int v = 0; v < 5; v++) acc[v] = (T)d.M[v * n + i];
-      for (int q = d.cf_ptr[i]; q < d.cf_ptr[i + 1]; q++) {
-        int f = d.cf_face[q];
-        int L = d.fL[f], R = d.fR[f];
-        if (R < 0) continue;                 // ghost increments are zero in this sweep
-        bool own = (L == i);
-        int j = own ? R : L;
-        if (j >= i) continue;
-        T sg = own ? (T)1 : (T)-1;
-        T nx = sg * (T)d.fnx[f], ny = sg * (T)d.fny[f];
-        T hS = (T)0.5 * (T)d.fS[f], lam = (T)d.lam_f[f];
+    for (int v = 0; v < 5; v++) rf[v * P + pf] = (T)d.M[v * n + i];
+    rf[5 * P + pf] = (T)r; rf[6 * P + pf] = (T)mx; rf[7 * P + pf] = (T)my;
 #pragma unroll
-        for (int v = 0; v < 4; v++) {
-          T dfn = dF[(2 * v) * n + j] * nx + dF[(2 * v + 1) * n + j] * ny;
-          acc[v] -= hS * (dfn - lam * dWs[v * n + j]);
-        }
-        if (fl.sa_on) acc[4] -= (T)d.sa_a[(own ? 0 : 1) * nf + f] * dWs[4 * n + j];
-      }
-      double Lam = d.Lam[i];
-      T D = (T)(Lam / cfl + Lam);
-      T dw[5];
+    for (int v = 0; v < 5; v++) { rf[(8 + v) * P + pf] = c[v * n + i]; rb[(5 + v) * P + pb] = c[v * n + i]; }
 #pragma unroll
-      for (int v = 0; v < 4; v++) dw[v] = acc[v] / D;
-      dw[4] = fl.sa_on ? acc[4] / (T)(Lam / cfl + d.sa_diag[i]) : (T)0;
-#pragma unroll
-      for (int v = 0; v < 5; v++) dWs[v * n + i] = dw[v];
-      T o[8];
-      delta_flux<T>((T)d.W[i], (T)d.W[n + i], (T)d.W[2 * n + i], (T)d.W[3 * n + i], dw[0], dw[1], dw[2], dw[3], o);
-#pragma unroll
-      for (int c = 0; c < 8; c++) dF[c * n + i] = o[c];
+    for (int v = 0; v < 5; v++) rb[v * P + pb] = (T)d.W[v * n + i];
+  }
+  T* sc = (T*)d.sw_st;
+  const int nnz = d.nnz;
+  for (int k = d.cf_ptr[i]; k < d.cf_ptr[i + 1]; k++) {
+    const int f = d.cf_face[k];
+    const bool own = (d.fL[f] == i);
+    const int j = own ? d.fR[f] : d.fL[f];
+    const double hS = 0.5 * d.fS[f];
+    const double sg = own ? hS : -hS;
+    d.sw_j[k] = j;                                    // -1 on a boundary face
+    sc[k] = (T)(sg * d.fnx[f]);
+    sc[nnz + k] = (T)(sg * d.fny[f]);
+    sc[2 * nnz + k] = (T)(hS * d.lam_f[f]);
+    sc[3 * nnz + k] = (T)d.sa_a[(own ? 0 : 1) * nf + f];
+    // the same coefficients in sweep-position order for the narrow schedule
+    const int ef = d.cf_to_fs[k], eb = d.cf_to_bs[k];
+    if (ef >= 0) {
+      T* o = (T*)d.sc_f;
+      o[ef] = sc[k]; o[d.nfs + ef] = sc[nnz + k]; o[2 * d.nfs + ef] = sc[2 * nnz + k]; o[3 * d.nfs + ef] = sc[3 * nnz + k];
     }
-    __syncthreads();
+    if (eb >= 0) {
+      T* o = (T*)d.sc_b;
+      o[eb] = sc[k]; o[d.nbs + eb] = sc[nnz + k]; o[2 * d.nbs + eb] = sc[2 * nnz + k]; o[3 * d.nbs + eb] = sc[3 * nnz + k];
+    }
+    const size_t PE = (size_t)PF_E * d.npos;
+    const int xf = d.cf_to_ef[k], xb = d.cf_to_eb[k];
+    if (xf >= 0) {
+      T* o = (T*)d.ec_f;
+      o[xf] = sc[k]; o[PE + xf] = sc[nnz + k]; o[2 * PE + xf] = sc[2 * nnz + k]; o[3 * PE + xf] = sc[3 * nnz + k];
+    }
+    if (xb >= 0) {
+      T* o = (T*)d.ec_b;
+      o[xb] = sc[k]; o[PE + xb] = sc[nnz + k]; o[2 * PE + xb] = sc[2 * nnz + k]; o[3 * PE + xb] = sc[3 * nnz + k];
+    }
   }
 }
 
+// ---- one cell of the forward sweep (wide schedule, stencil in cell-face order) ----
 template <class T>
-__global__ void k_sweep_bwd(Dev d) {
-  const int s = blockIdx.x;
-  SolveState& st = d.st[s];
-  if (st.state != 0) return;
-  const DevFlow& fl = d.flow[s];
-  const int n = d.nc_pad, nf = d.nf;
-  const double cfl = st.cfl;
+__device__ __forceinline__ void fwd_cell(const Dev& d, int i, bool sa_on) {
+  const int n = d.nc_pad, nnz = d.nnz;
   T* dWs = (T*)d.dWs;
+  T* dF = (T*)d.dF;
+  const T* c = (const T*)d.sw_cell;
+  const T* sc = (const T*)d.sw_st;
+  T acc[5];
+#pragma unroll
+  for (int v = 0; v < 5; v++) acc[v] = (T)d.M[v * n + i];
+  for (int k = d.cf_ptr[i]; k < d.cf_ptr[i + 1]; k++) {
+    const int j = d.sw_j[k];
+    if (j < 0 || j >= i) continue;                   // ghost increments are zero forward
+    T f[8], w[5];
+#pragma unroll
+    for (int q = 0; q < 8; q++) f[q] = dF[q * n + j];
+#pragma unroll
+    for (int v = 0; v < 5; v++) w[v] = dWs[v * n + j];
+    fwd_acc<T>(acc, sc[k], sc[nnz + k], sc[2 * nnz + k], sc[3 * nnz + k], f, w, sa_on);
+  }
+  T dw[5];
+#pragma unroll
+  for (int v = 0; v < 4; v++) dw[v] = acc[v] * c[i];
+  dw[4] = sa_on ? acc[4] * c[n + i] : (T)0;
+#pragma unroll
+  for (int v = 0; v < 5; v++) dWs[v * n + i] = dw[v];
+  T o[8];
+  delta_flux<T>((T)d.W[i], (T)d.W[n + i], (T)d.W[2 * n + i], c[2 * n + i], c[3 * n + i], c[4 * n + i],
+                dw[0], dw[1], dw[2], dw[3], o);
+#pragma unroll
+  for (int q = 0; q < 8; q++) dF[q * n + i] = o[q];
+}
+
+__device__ __forceinline__ void flush_eq40(const Dev& d, int s, double eq40, int bad);
+
+template <class T>
+__device__ __forceinline__ void bwd_entry(const Dev& d, const T* ring, const T* dF, const T* dWo, int j, int slot,
+                                          const T* ws, T sx, T sy, T sl, T sa, bool sa_on, T* acc);
+
+// ---- one cell of the backward sweep (wide schedule, stencil in cell-face order) ----
+template <class T>
+__device__ __forceinline__ void bwd_cell(const Dev& d, int i, bool sa_on) {
+  const int n = d.nc_pad, nnz = d.nnz;
+  const T* dWs = (const T*)d.dWs;
   T* dWo = (T*)d.dW;
   T* dF = (T*)d.dF;
+  const T* c = (const T*)d.sw_cell;
+  const T* sc = (const T*)d.sw_st;
+  T ws[5];
+#pragma unroll
+  for (int v = 0; v < 5; v++) ws[v] = dWs[v * n + i];
+  T acc[5] = {0, 0, 0, 0, 0};
+  for (int k = d.cf_ptr[i]; k < d.cf_ptr[i + 1]; k++) {
+    int j = d.sw_j[k];
+    if (j >= 0) {
+      if (j <= i) continue;
+    } else {
+      const int f = d.cf_face[k];
+      if (d.fbc[f] == 1) continue;                   // far-field increments are zero
+      j = -1 - f;
+    }
+    bwd_entry<T>(d, nullptr, dF, dWo, j, -1, ws, sc[k], sc[nnz + k], sc[2 * nnz + k], sc[3 * nnz + k], sa_on, acc);
+  }
+  T dw[5];
+#pragma unroll
+  for (int v = 0; v < 4; v++) { dw[v] = ws[v] - acc[v] * c[i]; dWo[v * n + i] = dw[v]; }
+  dw[4] = sa_on ? ws[4] - acc[4] * c[n + i] : (T)0;
+  dWo[4 * n + i] = dw[4];
+  T o[8];
+  delta_flux<T>((T)d.W[i], (T)d.W[n + i], (T)d.W[2 * n + i], c[2 * n + i], c[3 * n + i], c[4 * n + i],
+                dw[0], dw[1], dw[2], dw[3], o);
+#pragma unroll
+  for (int q = 0; q < 8; q++) dF[q * n + i] = o[q];
+}
+
+// ---- state update W += dW (FP64), nu_tilde floor, Eq. 40 ratio, divergence check ----
+// Runs after the backward sweep over all cells at once: it is off the sweeps' dependency
+// chain, and its FP64 square roots and division are spread over the whole GPU.
+template <class T>
+__global__ void __launch_bounds__(CELL_BLOCK) k_update(Dev d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = d.cell_solve[blockIdx.x * CELL_BLOCK];   // every block lies in one solve
   double eq40 = 0.0;
   int bad = 0;
-  const int l0 = d.blvl_solve_ptr[s], l1 = d.blvl_solve_ptr[s + 1] - 1;
-  for (int l = l0; l < l1; l++) {
-    int b = d.bwd_lvl[l], e = d.bwd_lvl[l + 1];
-    for (int k = b + threadIdx.x; k < e; k += blockDim.x) {
-      int i = d.bwd_order[k];
-      T ws[5];
+  const bool live = (i < d.nc_pad) && d.cell_solve[i] >= 0 && d.st[d.cell_solve[i]].state == 0;
+  if (live) {
+    const int n = d.nc_pad;
+    const T* dWo = (const T*)d.dW;
+    double Wi[5];
 #pragma unroll
-      for (int v = 0; v < 5; v++) ws[v] = dWs[v * n + i];
-      T acc[5] = {0, 0, 0, 0, 0};
-      for (int q = d.cf_ptr[i]; q < d.cf_ptr[i + 1]; q++) {
-        int f = d.cf_face[q];
-        int L = d.fL[f], R = d.fR[f];
-        bool own = (L == i);
-        T sg = own ? (T)1 : (T)-1;
-        T nx = sg * (T)d.fnx[f], ny = sg * (T)d.fny[f];
-        T hS = (T)0.5 * (T)d.fS[f], lam = (T)d.lam_f[f];
-        if (R < 0) {
-          int bc = d.fbc[f];
-          if (bc == 1) continue;             // far-field increments are zero
-          // wall / symmetry ghost: boundary map of the cell's own forward increment
-          T g[5];
-          g[0] = ws[0]; g[3] = ws[3];
-          if (bc == 3) { g[1] = -ws[1]; g[2] = -ws[2]; g[4] = -ws[4]; }
-          else {
-            T fnx = (T)d.fnx[f], fny = (T)d.fny[f];
-            T mn = ws[1] * fnx + ws[2] * fny;
-            g[1] = ws[1] - (T)2 * mn * fnx; g[2] = ws[2] - (T)2 * mn * fny; g[4] = ws[4];
-          }
-          T o[8];
-          delta_flux<T>((T)d.G[f], (T)d.G[nf + f], (T)d.G[2 * nf + f], (T)d.G[3 * nf + f], g[0], g[1], g[2], g[3], o);
+    for (int v = 0; v < 5; v++) Wi[v] = d.W[v * n + i];
+    double num = 0.0, den = 0.0;
 #pragma unroll
-          for (int v = 0; v < 4; v++) acc[v] += hS * ((o[2 * v] * nx + o[2 * v + 1] * ny) - lam * g[v]);
-          if (fl.sa_on) acc[4] += (T)d.sa_a[f] * g[4];
-          continue;
-        }
-        int j = own ? R : L;
-        if (j <= i) continue;
-#pragma unroll
-        for (int v = 0; v < 4; v++) {
-          T dfn = dF[(2 * v) * n + j] * nx + dF[(2 * v + 1) * n + j] * ny;
-          acc[v] += hS * (dfn - lam * dWo[v * n + j]);
-        }
-        if (fl.sa_on) acc[4] += (T)d.sa_a[(own ? 0 : 1) * nf + f] * dWo[4 * n + j];
-      }
-      double Lam = d.Lam[i];
-      T D = (T)(Lam / cfl + Lam);
-      T dw[5];
-#pragma unroll
-      for (int v = 0; v < 4; v++) dw[v] = ws[v] - acc[v] / D;
-      dw[4] = fl.sa_on ? ws[4] - acc[4] / (T)(Lam / cfl + d.sa_diag[i]) : (T)0;
-#pragma unroll
-      for (int v = 0; v < 5; v++) dWo[v * n + i] = dw[v];
-      double Wi[5];
-#pragma unroll
-      for (int v = 0; v < 5; v++) Wi[v] = d.W[v * n + i];
-      T o[8];
-      delta_flux<T>((T)Wi[0], (T)Wi[1], (T)Wi[2], (T)Wi[3], dw[0], dw[1], dw[2], dw[3], o);
-#pragma unroll
-      for (int c = 0; c < 8; c++) dF[c * n + i] = o[c];
-      // update (FP64) and the Eq. 40 ratio
-      double num = 0.0, den = 0.0;
-#pragma unroll
-      for (int v = 0; v < 4; v++) {
-        double dv = (double)dw[v];
-        num += dv * dv;
-        den += Wi[v] * Wi[v];
-        Wi[v] += dv;
-      }
-      Wi[4] += (double)dw[4];
-      if (Wi[4] < 0.0) Wi[4] = 0.0;
-      eq40 = fmax(eq40, sqrt(num) / sqrt(den));
-      double p = pressure_of(Wi[0], Wi[1], Wi[2], Wi[3]);
-      if (!(Wi[0] > 0.0) || !(p > 0.0) || !isfinite(Wi[3]) || !isfinite(Wi[4])) bad = 1;
-#pragma unroll
-      for (int v = 0; v < 5; v++) d.W[v * n + i] = Wi[v];
+    for (int v = 0; v < 4; v++) {
+      const double dv = (double)dWo[v * n + i];
+      num += dv * dv;
+      den += Wi[v] * Wi[v];
+      Wi[v] += dv;
     }
-    __syncthreads();
+    Wi[4] += (double)dWo[4 * n + i];
+    if (Wi[4] < 0.0) Wi[4] = 0.0;
+    eq40 = sqrt(num) / sqrt(den);
+    const double p = pressure_of(Wi[0], Wi[1], Wi[2], Wi[3]);
+    if (!(Wi[0] > 0.0) || !(p > 0.0) || !isfinite(Wi[3]) || !isfinite(Wi[4])) bad = 1;
+#pragma unroll
+    for (int v = 0; v < 5; v++) d.W[v * n + i] = Wi[v];
   }
-  // block reductions of the Eq. 40 ratio and the divergence flag
+  flush_eq40(d, (s >= 0 && d.st[s].state == 0) ? s : -1, eq40, bad);
+}
+
+// block-wide max of the Eq. 40 ratio and OR of the divergence flag, one atomic each;
+// positive doubles order like their bit patterns, so the per-solve maximum is exact
+__device__ __forceinline__ void flush_eq40(const Dev& d, int s, double eq40, int bad) {
   __shared__ double sm[32];
   __shared__ int sb[32];
   for (int o = 16; o > 0; o >>= 1) {
@@ -191,21 +261,422 @@ __global__ void k_sweep_bwd(Dev d) {
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = 0.0;
-    int bb = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) { a = fmax(a, sm[w]); bb |= sb[w]; }
-    st.eq40 = a;
-    if (bb) st.pending = -5;
+    int b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) { a = fmax(a, sm[w]); b |= sb[w]; }
+    if (s >= 0) {
+      if (a > 0.0) atomicMax(d.eq40_bits + s, (unsigned long long)__double_as_longlong(a));
+      if (b) atomicOr(d.bad + s, 1);
+    }
   }
 }
 
+// ---- narrow schedule: one block per solve, shared-memory ring of recent increments ----
+// ring layout: [13][RING] of T: the 8 flux increments, then the 5 variable increments of
+// the cell at sweep position p (local to the solve), stored at slot p % RING.
+//
+// Per-position records (written by the pre-pass, position-major SoA so one level's
+// records are contiguous) are prefetched into registers one level ahead: the block
+// issues the loads of level l+1 before it works on level l, so by the time level l+1
+// starts only the neighbours' increments (shared-memory ring) sit on the dependency chain.
+template <class T>
+__device__ __forceinline__ void ring_put(T* ring, int slot, const T* o, const T* dw) {
+#pragma unroll
+  for (int q = 0; q < 8; q++) ring[q * RING + slot] = o[q];
+#pragma unroll
+  for (int v = 0; v < 5; v++) ring[(8 + v) * RING + slot] = dw[v];
+}
+
+template <class T>
+__device__ __forceinline__ void neighbour(const Dev& d, const T* ring, const T* dF, const T* dWv, int j, int slot,
+                                          T* f, T* w) {
+  const int n = d.nc_pad;
+  if (slot >= 0) {
+#pragma unroll
+    for (int k = 0; k < 8; k++) f[k] = ring[k * RING + slot];
+#pragma unroll
+    for (int v = 0; v < 5; v++) w[v] = ring[(8 + v) * RING + slot];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; k++) f[k] = dF[k * n + j];
+#pragma unroll
+    for (int v = 0; v < 5; v++) w[v] = dWv[v * n + j];
+  }
+}
+
+// Each cell of a level is handled by one thread. Its record (per-iteration data and up
+// to PF_E stencil entries) is staged into shared memory by cp.async one level ahead.
+
+// asynchronous global -> shared copies (cp.async, 4 or 8 bytes): the copy proceeds in the
+// background and never holds registers, so the next level's records are in flight while
+// the current level is computed
+template <class U>
+__device__ __forceinline__ void cpa(U* dst_smem, const U* src) {
+  static_assert(sizeof(U) == 4 || sizeof(U) == 8, "cp.async element size");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst_smem);
+  if (sizeof(U) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// forward record of one position: residual, state (r, mx, my), 1/D, 1/a_ii, u, v, H, cell,
+// entry count, backward position, and PF_E stencil entries
+template <class T>
+struct FwdRec {
+  T m[5], w[3], c[5];
+  T co[4][PF_E];
+  int i, cnt, pb, pad;
+  int j[PF_E], slot[PF_E];
+};
+
+template <class T>
+__device__ __forceinline__ void fwd_stage(const Dev& d, int p, FwdRec<T>* st) {
+  const int P = d.npos;
+  const T* rec = (const T*)d.rec_f;
+  const T* ec = (const T*)d.ec_f;
+#pragma unroll
+  for (int v = 0; v < 5; v++) cpa(&st->m[v], rec + v * P + p);
+#pragma unroll
+  for (int v = 0; v < 3; v++) cpa(&st->w[v], rec + (5 + v) * P + p);
+#pragma unroll
+  for (int v = 0; v < 5; v++) cpa(&st->c[v], rec + (8 + v) * P + p);
+  cpa(&st->i, d.fwd_order + p);
+  cpa(&st->cnt, d.cnt_f + p);
+  cpa(&st->pb, d.pb_of_pf + p);
+#pragma unroll
+  for (int e = 0; e < PF_E; e++) {
+    cpa(&st->j[e], d.ej_f + e * P + p);
+    cpa(&st->slot[e], d.eslot_f + e * P + p);
+#pragma unroll
+    for (int k = 0; k < 4; k++) cpa(&st->co[k][e], ec + (k * PF_E + e) * P + p);
+  }
+  cpa_commit();
+}
+
+template <class T>
+__device__ __forceinline__ void fwd_load_direct(const Dev& d, int p, FwdRec<T>* st) {
+  const int P = d.npos;
+  const T* rec = (const T*)d.rec_f;
+  const T* ec = (const T*)d.ec_f;
+#pragma unroll
+  for (int v = 0; v < 5; v++) st->m[v] = rec[v * P + p];
+#pragma unroll
+  for (int v = 0; v < 3; v++) st->w[v] = rec[(5 + v) * P + p];
+#pragma unroll
+  for (int v = 0; v < 5; v++) st->c[v] = rec[(8 + v) * P + p];
+  st->i = d.fwd_order[p];
+  st->cnt = d.cnt_f[p];
+  st->pb = d.pb_of_pf[p];
+#pragma unroll
+  for (int e = 0; e < PF_E; e++) {
+    st->j[e] = d.ej_f[e * P + p];
+    st->slot[e] = d.eslot_f[e * P + p];
+#pragma unroll
+    for (int k = 0; k < 4; k++) st->co[k][e] = ec[(k * PF_E + e) * P + p];
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void fwd_process(const Dev& d, T* ring, int p, int pbase, const FwdRec<T>* r, bool sa_on) {
+  const int n = d.nc_pad, P = d.npos;
+  T* dWs = (T*)d.dWs;
+  T* dF = (T*)d.dF;
+  T acc[5];
+#pragma unroll
+  for (int v = 0; v < 5; v++) acc[v] = r->m[v];
+  const int cnt = r->cnt;
+  if (cnt >= 0) {
+#pragma unroll
+    for (int e = 0; e < PF_E; e++) {
+      if (e >= cnt) break;
+      T f[8], w[5];
+      neighbour<T>(d, ring, dF, dWs, r->j[e], r->slot[e], f, w);
+      fwd_acc<T>(acc, r->co[0][e], r->co[1][e], r->co[2][e], r->co[3][e], f, w, sa_on);
+    }
+  } else {
+    // more entries than the record holds: the position-ordered CSR stencil
+    const T* sc = (const T*)d.sc_f;
+    const int nfs = d.nfs;
+    for (int k = d.fs_ptr[p]; k < d.fs_ptr[p + 1]; k++) {
+      T f[8], w[5];
+      neighbour<T>(d, ring, dF, dWs, d.fs_j[k], d.fs_slot[k], f, w);
+      fwd_acc<T>(acc, sc[k], sc[nfs + k], sc[2 * nfs + k], sc[3 * nfs + k], f, w, sa_on);
+    }
+  }
+  T dw[5];
+#pragma unroll
+  for (int v = 0; v < 4; v++) dw[v] = acc[v] * r->c[0];
+  dw[4] = sa_on ? acc[4] * r->c[1] : (T)0;
+  T o[8];
+  delta_flux<T>(r->w[0], r->w[1], r->w[2], r->c[2], r->c[3], r->c[4], dw[0], dw[1], dw[2], dw[3], o);
+  const int slot = (p - pbase) % RING;
+  ring_put<T>(ring, slot, o, dw);
+  const int i = r->i, pb = r->pb;
+  T* recb = (T*)d.rec_b;
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    dWs[v * n + i] = dw[v];
+    recb[(10 + v) * P + pb] = dw[v];          // the backward sweep's copy of dW*
+  }
+#pragma unroll
+  for (int k = 0; k < 8; k++) dF[k * n + i] = o[k];
+}
+
+template <class T>
+__global__ void __launch_bounds__(NARROW_THREADS) k_sweep_fwd_narrow(Dev d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ring = (T*)smem_raw;
+  FwdRec<T>* stage = (FwdRec<T>*)(smem_raw + (size_t)13 * RING * sizeof(T));
+  FwdRec<T>* st = stage + threadIdx.x;               // staged record of this thread's next position
+  const int s = blockIdx.x;
+  if (d.st[s].state != 0) return;
+  const bool sa_on = d.flow[s].sa_on;
+  const int l0 = d.lvl_solve_ptr[s], l1 = d.lvl_solve_ptr[s + 1] - 1;
+  const int pbase = d.fwd_lvl[l0];
+  if (l0 < l1 && d.fwd_lvl[l0] + (int)threadIdx.x < d.fwd_lvl[l0 + 1]) fwd_stage<T>(d, d.fwd_lvl[l0] + threadIdx.x, st);
+  for (int l = l0; l < l1; l++) {
+    const int b = d.fwd_lvl[l], e = d.fwd_lvl[l + 1];
+    const bool mine = b + (int)threadIdx.x < e;
+    FwdRec<T> cur;
+    if (mine) {
+      cpa_wait_all();
+      cur = *st;                 // this level's record into registers, freeing the stage
+    }
+    // the next level's record is in flight while this level is computed
+    if (l + 1 < l1 && e + (int)threadIdx.x < d.fwd_lvl[l + 2]) fwd_stage<T>(d, e + threadIdx.x, st);
+    if (mine) fwd_process<T>(d, ring, b + threadIdx.x, pbase, &cur, sa_on);
+    for (int p = b + threadIdx.x + blockDim.x; p < e; p += blockDim.x) {   // levels wider than the block
+      FwdRec<T> xt;
+      fwd_load_direct<T>(d, p, &xt);
+      fwd_process<T>(d, ring, p, pbase, &xt, sa_on);
+    }
+    __syncthreads();
+  }
+}
+
+// backward record: state (5), 1/D, 1/a_ii, u, v, H, the forward increment dW* (5), cell,
+// entry count and PF_E entries (upper neighbours, wall/symmetry ghosts)
+template <class T>
+struct BwdRec {
+  T w[5], c[5], ws[5];
+  T co[4][PF_E];
+  int i, cnt;
+  int j[PF_E], slot[PF_E];
+};
+
+template <class T>
+__device__ __forceinline__ void bwd_stage(const Dev& d, int p, BwdRec<T>* st) {
+  const int P = d.npos;
+  const T* rec = (const T*)d.rec_b;
+  const T* ec = (const T*)d.ec_b;
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    cpa(&st->w[v], rec + v * P + p);
+    cpa(&st->c[v], rec + (5 + v) * P + p);
+    cpa(&st->ws[v], rec + (10 + v) * P + p);
+  }
+  cpa(&st->i, d.bwd_order + p);
+  cpa(&st->cnt, d.cnt_b + p);
+#pragma unroll
+  for (int e = 0; e < PF_E; e++) {
+    cpa(&st->j[e], d.ej_b + e * P + p);
+    cpa(&st->slot[e], d.eslot_b + e * P + p);
+#pragma unroll
+    for (int k = 0; k < 4; k++) cpa(&st->co[k][e], ec + (k * PF_E + e) * P + p);
+  }
+  cpa_commit();
+}
+
+template <class T>
+__device__ __forceinline__ void bwd_load_direct(const Dev& d, int p, BwdRec<T>* st) {
+  const int P = d.npos;
+  const T* rec = (const T*)d.rec_b;
+  const T* ec = (const T*)d.ec_b;
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    st->w[v] = rec[v * P + p];
+    st->c[v] = rec[(5 + v) * P + p];
+    st->ws[v] = rec[(10 + v) * P + p];
+  }
+  st->i = d.bwd_order[p];
+  st->cnt = d.cnt_b[p];
+#pragma unroll
+  for (int e = 0; e < PF_E; e++) {
+    st->j[e] = d.ej_b[e * P + p];
+    st->slot[e] = d.eslot_b[e * P + p];
+#pragma unroll
+    for (int k = 0; k < 4; k++) st->co[k][e] = ec[(k * PF_E + e) * P + p];
+  }
+}
+
+// contribution of one backward entry: upper neighbour j (its increments from the ring or
+// global memory), or a wall/symmetry ghost (j = -1 - face: boundary map of this cell's
+// own forward increment ws, flux increment about the ghost state)
+template <class T>
+__device__ __forceinline__ void bwd_entry(const Dev& d, const T* ring, const T* dF, const T* dWo, int j, int slot,
+                                          const T* ws, T sx, T sy, T sl, T sa, bool sa_on, T* acc) {
+  T f[8], w[5];
+  if (j >= 0) {
+    neighbour<T>(d, ring, dF, dWo, j, slot, f, w);
+  } else {
+    const int nf = d.nf, fc = -1 - j;
+    w[0] = ws[0]; w[3] = ws[3];
+    if (d.fbc[fc] == 3) { w[1] = -ws[1]; w[2] = -ws[2]; w[4] = -ws[4]; }
+    else {
+      const T fx = (T)d.fnx[fc], fy = (T)d.fny[fc];
+      const T mn = ws[1] * fx + ws[2] * fy;
+      w[1] = ws[1] - (T)2 * mn * fx; w[2] = ws[2] - (T)2 * mn * fy; w[4] = ws[4];
+    }
+    const double gr = d.G[fc], gmx = d.G[nf + fc], gmy = d.G[2 * nf + fc], gE = d.G[3 * nf + fc];
+    const double gu = gmx / gr, gv = gmy / gr;
+    const double gp = (GAMMA - 1.0) * (gE - 0.5 * (gmx * gu + gmy * gv));
+    delta_flux<T>((T)gr, (T)gmx, (T)gmy, (T)gu, (T)gv, (T)(gE + gp), w[0], w[1], w[2], w[3], f);
+  }
+  bwd_acc<T>(acc, sx, sy, sl, sa, f, w, sa_on);
+}
+
+template <class T>
+__device__ __forceinline__ void bwd_process(const Dev& d, T* ring, int p, int pbase, const BwdRec<T>* r, bool sa_on) {
+  const int n = d.nc_pad;
+  T* dWo = (T*)d.dW;
+  T* dF = (T*)d.dF;
+  T ws[5];
+#pragma unroll
+  for (int v = 0; v < 5; v++) ws[v] = r->ws[v];
+  T acc[5] = {0, 0, 0, 0, 0};
+  const int cnt = r->cnt;
+  if (cnt >= 0) {
+#pragma unroll
+    for (int e = 0; e < PF_E; e++) {
+      if (e >= cnt) break;
+      bwd_entry<T>(d, ring, dF, dWo, r->j[e], r->slot[e], ws, r->co[0][e], r->co[1][e], r->co[2][e], r->co[3][e],
+                   sa_on, acc);
+    }
+  } else {
+    const T* sc = (const T*)d.sc_b;
+    const int nbs = d.nbs;
+    for (int k = d.bs_ptr[p]; k < d.bs_ptr[p + 1]; k++)
+      bwd_entry<T>(d, ring, dF, dWo, d.bs_j[k], d.bs_slot[k], ws, sc[k], sc[nbs + k], sc[2 * nbs + k],
+                   sc[3 * nbs + k], sa_on, acc);
+  }
+  T dw[5];
+#pragma unroll
+  for (int v = 0; v < 4; v++) dw[v] = ws[v] - acc[v] * r->c[0];
+  dw[4] = sa_on ? ws[4] - acc[4] * r->c[1] : (T)0;
+  T o[8];
+  delta_flux<T>(r->w[0], r->w[1], r->w[2], r->c[2], r->c[3], r->c[4], dw[0], dw[1], dw[2], dw[3], o);
+  ring_put<T>(ring, (p - pbase) % RING, o, dw);
+  const int i = r->i;
+#pragma unroll
+  for (int v = 0; v < 5; v++) dWo[v * n + i] = dw[v];
+#pragma unroll
+  for (int k = 0; k < 8; k++) dF[k * n + i] = o[k];
+}
+
+template <class T>
+__global__ void __launch_bounds__(NARROW_THREADS) k_sweep_bwd_narrow(Dev d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ring = (T*)smem_raw;
+  BwdRec<T>* stage = (BwdRec<T>*)(smem_raw + (size_t)13 * RING * sizeof(T));
+  BwdRec<T>* st = stage + threadIdx.x;
+  const int s = blockIdx.x;
+  if (d.st[s].state != 0) return;
+  const bool sa_on = d.flow[s].sa_on;
+  const int l0 = d.blvl_solve_ptr[s], l1 = d.blvl_solve_ptr[s + 1] - 1;
+  const int pbase = d.bwd_lvl[l0];
+  if (l0 < l1 && d.bwd_lvl[l0] + (int)threadIdx.x < d.bwd_lvl[l0 + 1]) bwd_stage<T>(d, d.bwd_lvl[l0] + threadIdx.x, st);
+  for (int l = l0; l < l1; l++) {
+    const int b = d.bwd_lvl[l], e = d.bwd_lvl[l + 1];
+    const bool mine = b + (int)threadIdx.x < e;
+    BwdRec<T> cur;
+    if (mine) {
+      cpa_wait_all();
+      cur = *st;
+    }
+    if (l + 1 < l1 && e + (int)threadIdx.x < d.bwd_lvl[l + 2]) bwd_stage<T>(d, e + threadIdx.x, st);
+    if (mine) bwd_process<T>(d, ring, b + threadIdx.x, pbase, &cur, sa_on);
+    for (int p = b + threadIdx.x + blockDim.x; p < e; p += blockDim.x) {   // levels wider than the block
+      BwdRec<T> xt;
+      bwd_load_direct<T>(d, p, &xt);
+      bwd_process<T>(d, ring, p, pbase, &xt, sa_on);
+    }
+    __syncthreads();
+  }
+}
+
+// ---- wide schedule: one launch per level, all solves ----
+template <class T>
+__global__ void k_sweep_fwd_level(Dev d, int b, int e) {
+  const int k = b + blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= e) return;
+  const int i = d.wfwd_cells[k];
+  const int s = d.cell_solve[i];
+  if (d.st[s].state != 0) return;
+  fwd_cell<T>(d, i, d.flow[s].sa_on);
+}
+
+template <class T>
+__global__ void k_sweep_bwd_level(Dev d, int b, int e) {
+  const int k = b + blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= e) return;
+  const int i = d.wbwd_cells[k];
+  const int s = d.cell_solve[i];
+  if (d.st[s].state != 0) return;
+  bwd_cell<T>(d, i, d.flow[s].sa_on);
+}
+
+constexpr int WIDE_BLOCK = 128;
+
+void launch_update(const Dev& d, int precision, cudaStream_t s) {
+  if (precision == 1) k_update<float><<<d.n_cell_blocks, CELL_BLOCK, 0, s>>>(d);
+  else k_update<double><<<d.n_cell_blocks, CELL_BLOCK, 0, s>>>(d);
+}
+
+// dynamic shared memory of the narrow sweeps: the ring plus one staged record per thread
+// (one staged record per thread)
+template <class T>
+static size_t fwd_smem() { return (size_t)13 * RING * sizeof(T) + (size_t)NARROW_THREADS * sizeof(FwdRec<T>); }
+template <class T>
+static size_t bwd_smem() { return (size_t)13 * RING * sizeof(T) + (size_t)NARROW_THREADS * sizeof(BwdRec<T>); }
+
+void setup_sweeps() {
+  cudaFuncSetAttribute(k_sweep_fwd_narrow<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<double>());
+  cudaFuncSetAttribute(k_sweep_bwd_narrow<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<double>());
+  cudaFuncSetAttribute(k_sweep_fwd_narrow<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<float>());
+  cudaFuncSetAttribute(k_sweep_bwd_narrow<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<float>());
+}
+
+void launch_sweep_prep(const Dev& d, int precision, cudaStream_t s) {
+  if (precision == 1) k_sweep_prep<float><<<d.n_cell_blocks, CELL_BLOCK, 0, s>>>(d);
+  else k_sweep_prep<double><<<d.n_cell_blocks, CELL_BLOCK, 0, s>>>(d);
+}
+
 void launch_sweep_fwd(const Dev& d, int precision, int threads, cudaStream_t s) {
-  if (precision == 1) k_sweep_fwd<float><<<d.n_solves, threads, 0, s>>>(d);
-  else k_sweep_fwd<double><<<d.n_solves, threads, 0, s>>>(d);
+  if (d.wide) {
+    for (int l = 0; l < d.n_wfwd; l++) {
+      const int b = d.h_wfwd_ptr[l], e = d.h_wfwd_ptr[l + 1];
+      const int g = (e - b + WIDE_BLOCK - 1) / WIDE_BLOCK;
+      if (precision == 1) k_sweep_fwd_level<float><<<g, WIDE_BLOCK, 0, s>>>(d, b, e);
+      else k_sweep_fwd_level<double><<<g, WIDE_BLOCK, 0, s>>>(d, b, e);
+    }
+    return;
+  }
+  if (precision == 1) k_sweep_fwd_narrow<float><<<d.n_solves, threads, fwd_smem<float>(), s>>>(d);
+  else k_sweep_fwd_narrow<double><<<d.n_solves, threads, fwd_smem<double>(), s>>>(d);
 }
 
 void launch_sweep_bwd(const Dev& d, int precision, int threads, cudaStream_t s) {
-  if (precision == 1) k_sweep_bwd<float><<<d.n_solves, threads, 0, s>>>(d);
-  else k_sweep_bwd<double><<<d.n_solves, threads, 0, s>>>(d);
+  if (d.wide) {
+    for (int l = 0; l < d.n_wbwd; l++) {
+      const int b = d.h_wbwd_ptr[l], e = d.h_wbwd_ptr[l + 1];
+      const int g = (e - b + WIDE_BLOCK - 1) / WIDE_BLOCK;
+      if (precision == 1) k_sweep_bwd_level<float><<<g, WIDE_BLOCK, 0, s>>>(d, b, e);
+      else k_sweep_bwd_level<double><<<g, WIDE_BLOCK, 0, s>>>(d, b, e);
+    }
+    return;
+  }
+  if (precision == 1) k_sweep_bwd_narrow<float><<<d.n_solves, threads, bwd_smem<float>(), s>>>(d);
+  else k_sweep_bwd_narrow<double><<<d.n_solves, threads, bwd_smem<double>(), s>>>(d);
 }
 
 }  // namespace igks

@@ -27,7 +27,7 @@ class IgksError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
                 ("check_every", C.c_int32), ("use_graph", C.c_int32), ("sweep_threads", C.c_int32),
-                ("timing", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("timing", C.c_int32), ("sweep_mode", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class Flow(C.Structure):
@@ -81,6 +81,8 @@ def lib():
         L.igks_kernel_name.restype = C.c_char_p
         L.igks_residual_norms_noalloc.argtypes = [vp, vp, i32, vp, vp]
         L.igks_residual_norms_noalloc.restype = C.c_int32
+        L.igks_order_cells.argtypes = [i32, i32, ip, i32, ip, ip]
+        L.igks_order_cells.restype = C.c_int32
         for name in ("igks_create", "igks_mesh_upload", "igks_set_flow", "igks_init_freestream",
                      "igks_iterate", "igks_get_fields", "igks_set_fields", "igks_get_scalars",
                      "igks_set_scalars", "igks_get_array", "igks_mesh_info", "igks_get_forces",
@@ -108,6 +110,21 @@ def residual_norms_noalloc(m_rho_ptr: int, area_ptr: int, n_cells: int, out_ptr:
     return rc
 
 
+ORDER_AS_GIVEN, ORDER_MULTICOLOR = 0, 1
+
+
+def order_cells(mesh, mode=ORDER_MULTICOLOR):
+    """igks_order_cells: a cell permutation (perm[k] = old index at position k) and the
+    number of colours. Apply it with mesh.renumbered(perm) before upload."""
+    fc = np.ascontiguousarray(mesh.face_cells, dtype=np.int32).ravel()
+    perm = np.zeros(mesh.n_cells, dtype=np.int32)
+    nc = C.c_int32()
+    rc = lib().igks_order_cells(mesh.n_cells, mesh.n_faces, _ip(fc), mode, _ip(perm), C.byref(nc))
+    if rc != OK:
+        raise IgksError(rc, "igks_order_cells failed")
+    return perm, nc.value
+
+
 def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
@@ -129,9 +146,9 @@ class Context:
     """One igks_ctx: a set of steady solves resident on one GPU."""
 
     def __init__(self, precision=PREC_FP64, device=0, stream=None, check_every=20, use_graph=1,
-                 sweep_threads=0, timing=0):
+                 sweep_threads=0, timing=0, sweep_mode=0):
         o = Options(precision=precision, device=device, stream=stream, check_every=check_every,
-                    use_graph=use_graph, sweep_threads=sweep_threads, timing=timing)
+                    use_graph=use_graph, sweep_threads=sweep_threads, timing=timing, sweep_mode=sweep_mode)
         h = C.c_void_p()
         rc = lib().igks_create(C.byref(o), C.byref(h))
         if rc:

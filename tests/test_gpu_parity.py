@@ -180,3 +180,34 @@ def test_mesh_errors_are_reported():
     with pytest.raises(igks.IgksError) as e:
         ctx2.init_freestream(0)
     assert e.value.code == igks.EMESH
+
+
+@pytest.mark.parametrize("mk,flow_fn", [(G.laminar_plate, F.laminar_plate_flow),
+                                        (G.turbulent_plate, F.turbulent_plate_flow)])
+def test_multicolor_order_wide_sweeps_match_oracle(mk, flow_fn):
+    """Multicolour numbering (few, wide levels: one launch per level) on both sides."""
+    from paper_1709_00803_gb300 import igks
+    base = mk()
+    perm, ncol = igks.order_cells(base, igks.ORDER_MULTICOLOR)
+    m = base.renumbered(perm)
+    fl = flow_fn()
+    W0 = seeded(base, fl, 12)[:, perm]
+    ctx, sid, ora = make_pair(m, fl, W0)
+    info = ctx.mesh_info(sid)
+    assert info["levels_fwd"] <= ncol
+    assert ctx.launches_per_iteration() == 9 + info["levels_fwd"] + info["levels_bwd"]
+    ctx.iterate(1); ora.iterate(1)
+    _compare_iteration(ctx, sid, ora)
+    ctx.iterate(6); ora.iterate(6)
+    assert_close("W after 7", ctx.get_fields(sid), ora.get(O.ORA_W), TOL)
+
+
+def test_forced_wide_schedule_on_deep_ordering():
+    m = G.flat_plate_hybrid(nx=24, nq=8, ntri_rows=6, first=1e-5, seed=11)
+    fl = F.turbulent_plate_flow()
+    ctx, sid, ora = make_pair(m, fl, seeded(m, fl, 13), sweep_mode=2)
+    ctx.iterate(3); ora.iterate(3)
+    assert_close("W", ctx.get_fields(sid), ora.get(O.ORA_W), TOL)
+    ctx2, sid2, ora2 = make_pair(m, fl, seeded(m, fl, 13), sweep_mode=1, precision=1)
+    ctx2.iterate(1); ora2.iterate(1)
+    assert_close("dw fp32 narrow", ctx2.get_array(sid2, "dw")[:4], ora2.get(O.ORA_DW)[:4], 2e-5)
