@@ -7,12 +7,13 @@ both LU-SGS sweeps and the update) on a synthetic hybrid mesh.
 
 One step = one iteration of the whole hot path over one steady solve of the workload.
 `value` is device time (CUDA events on the library's stream around each step, L2 flushed
-between steps by writing a 256 MiB buffer outside the timed intervals); `e2e` is the same
-metric through the public API with host buffers: each step copies the state in from
-pinned host memory, iterates once (reading the per-solve status back) and copies the state
-out. Under torchrun each rank runs an independent replica (the method does not shard;
-replicas only) and rank 0 prints one JSON line with the max time over ranks.
---impl reference times the CPU oracle (single thread) on the same workload.
+between steps by writing a 256 MiB buffer outside the timed intervals) for the headline
+precision; the other precision is measured the same way and reported under "other".
+`e2e` is the same metric through the public API with host buffers: each step copies the
+state in from pinned host memory, iterates once (reading the per-solve status back) and
+copies the state out. Under torchrun each rank runs an independent replica (the method
+does not shard: replicas only) and rank 0 prints one JSON line with the max time over
+ranks. --impl reference times the CPU oracle (single thread) on the same workload.
 """
 from __future__ import annotations
 
@@ -41,20 +42,28 @@ WORKLOADS = {
     "naca0012": (G.naca0012, F.naca_flow, "NACA 0012, SA, Ma 0.15, Re 6e6, AoA 10, hybrid O-mesh"),
 }
 METRIC = "cell-updates/s"
+SM_COUNT, SM_MAX_GHZ = 152, 2.07
+# FP64 peak derived from unit counts and clock: 2 FP64 FMA per SM per clock (1.25 TFLOP/s
+# nominal) x 2 flop x 152 SMs x 2.07 GHz
+FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_GHZ / 1e3
+# Executed FP64 flops per face of k_flux (2 x DFMA + DADD + DMUL from ncu on the turbulent
+# plate, 35056 faces): the per-unit figure of its ALU roofline
+FLUX_FLOPS_PER_FACE = 3556.0
 
-# Algorithmic traffic per unit of each kernel (FP64 path): every array a kernel needs is
-# streamed once; neighbour re-reads are assumed to hit in cache. Units: cells or faces.
-# (bytes per unit, unit)
-ALG_BYTES = {
-    "k_gradient": (5 * 8 + 2 * 8 + 8 * 4 + 2 * 8 + (8 + 4) * 8 + 3 * 8, "cell"),
-    "k_flux": (2 * 4 + 9 * 8 + 2 * (5 + 12 + 2 + 2) * 8 + 10 * 8, "face"),
-    "k_residual": (8 + 6 * 8 + 5 * 8 + 5 * 8 + 4 * 8, "cell"),
-    "k_sweep_fwd": (8 + 5 * 8 + 4 * 8 + 5 * 8 + 8 * 8 + 2 * 8 + 8 * 4, "cell"),
-    "k_sweep_bwd": (8 + 5 * 8 + 5 * 8 + 5 * 8 + 8 * 8 + 5 * 8 + 2 * 8 + 8 * 4, "cell"),
-}
-# FP64 flops per face of the flux kernel, from ncu's executed FP64 instruction counts
-# (2 x DFMA + DADD + DMUL) on the same kernel; see the committed flux profile summary.
-FLUX_FLOPS_PER_FACE = None
+
+def alg_bytes(kernel, t, nc, nf):
+    """Algorithmic (compulsory) bytes of one launch: every array the kernel needs streamed
+    once, neighbour re-reads from cache. t = bytes of the sweep type."""
+    cell_flux_inputs = 21 * 8          # W 5, gradient 8, limiter 4, centroid 2, mu 2
+    per = {
+        "k_gradient": nc * (5 * 8 + 2 * 8 + 2 * 8 + 8 * 8 + 4 * 8 + 8 + 8 + 8) + nf * (2 * 4 + 5 * 8 + 8),
+        "k_flux": nf * (4 * 4 + 8 * 8 + 10 * 8) + nc * cell_flux_inputs,
+        "k_residual": nc * (8 + 8 * 8 + 5 * 8 + 3 * 8) + nf * (6 * 8 + 4 * 8),
+        "k_sweep_fwd": nc * (13 * t + 3 * 4 + 4 * (2 * 4 + 4 * t) + 18 * t),
+        "k_sweep_bwd": nc * (15 * t + 2 * 4 + 4 * (2 * 4 + 4 * t) + 13 * t),
+        "k_sweep_prep": nc * (5 * 8 + 8 + 8 + 23 * t) + nf * (6 * 8),
+    }
+    return per.get(kernel)
 
 
 def _dist():
@@ -124,7 +133,7 @@ def cpu_baseline(mesh, flow, budget_s=15.0):
     """The oracle as it stands, single-threaded, on the same workload (bounded sample)."""
     import oracle as O
     ora = O.Oracle(mesh, flow)
-    ora.iterate(1)   # first iteration (includes its own set-up costs)
+    ora.iterate(1)
     t0 = time.perf_counter()
     n = 0
     while True:
@@ -134,8 +143,8 @@ def cpu_baseline(mesh, flow, budget_s=15.0):
             break
     dt = time.perf_counter() - t0
     return {"value": mesh.n_cells * n / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"{n} iterations of the {mesh.n_cells}-cell workload from a converging state, "
-                      f"{dt:.1f} s, single-threaded C oracle (-O2 -ffp-contract=off)"}
+            "sample": f"{n} iterations (after the first) of the {mesh.n_cells}-cell workload from the free "
+                      f"stream, {dt:.1f} s, single-threaded C oracle (-O2 -ffp-contract=off)"}
 
 
 def run_reference(args, mesh, flow, desc):
@@ -161,38 +170,13 @@ def run_reference(args, mesh, flow, desc):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--impl", default="igks", choices=["igks", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="turbulent_plate", choices=list(WORKLOADS))
-    ap.add_argument("--ordering", default="as_given", choices=["as_given", "multicolor"],
-                    help="cell numbering = LU-SGS sweep order (the oracle baseline runs the same)")
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
-    mk, fl_fn, desc = WORKLOADS[args.workload]
-    mesh, flow = mk(), fl_fn()
-    if args.ordering == "multicolor":
-        from paper_1709_00803_gb300 import igks as _ig
-        perm, ncol = _ig.order_cells(mesh, _ig.ORDER_MULTICOLOR)
-        mesh = mesh.renumbered(perm)
-        desc += f", multicolour cell order ({ncol} colours)"
-    if args.impl == "reference":
-        return run_reference(args, mesh, flow, desc)
-
+def measure(args, mesh, flow, precision, dev, dist, ws, with_e2e):
+    """Time args.steps iterations of one solve at one sweep precision."""
     import torch
     from paper_1709_00803_gb300 import igks
 
-    dist, rank, ws = _dist()
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
-    prec = igks.PREC_MIXED if args.precision == "mixed" else igks.PREC_FP64
+    prec = igks.PREC_MIXED if precision == "mixed" else igks.PREC_FP64
     ctx = igks.Context(precision=prec, device=dev, stream=stream.cuda_stream, timing=1)
     sid = ctx.mesh_upload(mesh)
     ctx.set_flow(sid, flow)
@@ -220,74 +204,116 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = float(sum(step_ms))
+    total_ms = float(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
     if dist:
         t = torch.tensor([total_ms], device=f"cuda:{dev}")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     _, st = ctx.iterate(0)
-    value = ws * mesh.n_cells * args.steps / (total_ms / 1e3)
+    if st[sid]["state"] != 0 or st[sid]["iters"] != args.warmup + args.steps:
+        raise RuntimeError(f"the solve stopped during the timed steps: {st[sid]}")
+    res = {"value": ws * mesh.n_cells * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+           "kernel_ms": {k: round(statistics.mean(v), 5) for k, v in ktimes.items()},
+           "launches_per_step": ctx.launches_per_iteration(), "clocks": clk.summary(), "info": info,
+           "solver_state": {"iters": st[sid]["iters"], "res_l2_rel": st[sid]["res_l2_rel"], "cfl": st[sid]["cfl"]}}
+    if with_e2e:
+        W_host = torch.empty((5, mesh.n_cells), dtype=torch.float64).pin_memory().numpy()
+        ctx.get_fields(sid, out=W_host)
+        n_e2e = max(5, min(args.steps, 50))
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            ctx.set_fields(sid, W_host)          # H2D: the step's input state
+            ctx.iterate(1)                       # one iteration, per-solve status read back
+            ctx.get_fields(sid, out=W_host)      # D2H: the step's result
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e2e_s], device=f"cuda:{dev}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        res["e2e"] = {"value": ws * mesh.n_cells * n_e2e / e2e_s, "unit": METRIC,
+                      "h2d_bytes_per_step": int(W_host.nbytes), "d2h_bytes_per_step": int(W_host.nbytes) + 48}
+    ctx.destroy()
+    return res
 
-    # ---- end to end through the public API with host buffers ----
-    W_host = torch.empty((5, mesh.n_cells), dtype=torch.float64).pin_memory().numpy()
-    ctx.get_fields(sid, out=W_host)
-    e2e_steps = max(5, min(args.steps, 50))
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ctx.set_fields(sid, W_host)          # H2D: the step's input state
-        ctx.iterate(1)                       # one iteration, per-solve status read back
-        ctx.get_fields(sid, out=W_host)      # D2H: the step's result
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": ws * mesh.n_cells * e2e_steps / e2e_s, "unit": METRIC,
-           "h2d_bytes_per_step": int(W_host.nbytes), "d2h_bytes_per_step": int(W_host.nbytes) + 48}
 
-    # ---- roofline of the dominant kernel ----
-    kmean = {k: statistics.mean(v) for k, v in ktimes.items()}
-    dom = max(kmean, key=kmean.get)
+def rooflines(res, mesh, precision):
     peaks, src = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    roof = None
-    if dom == "k_flux" and FLUX_FLOPS_PER_FACE:
-        fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk x 2 flop x max clock
-        ach = FLUX_FLOPS_PER_FACE * mesh.n_faces / (kmean[dom] / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": ach / fp64_peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}
-    elif dom in ALG_BYTES:
-        b, unit = ALG_BYTES[dom]
-        units = mesh.n_faces if unit == "face" else mesh.n_cells
-        ach = b * units / (kmean[dom] / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "peak_source": f"hbm_gbs, {src}",
-                "alg_bytes_per_unit": b, "unit_of_work": unit}
-    clocks = clk.summary()
-    out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+    t = 4 if precision == "mixed" else 8
+    km = res["kernel_ms"]
+    dom = max(km, key=km.get)
+    b = alg_bytes(dom, t, mesh.n_cells, mesh.n_faces)
+    ach = b / (km[dom] / 1e3) / 1e9
+    dominant = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "peak_source": f"hbm_gbs ({src}, burst copy)",
+                "alg_bytes_per_launch": b, "note": "latency-bound dependency chain: one block walks the "
+                "sweep's levels; the HBM fraction shows how far it is from any bandwidth limit"}
+    flux_t = km["k_flux"]
+    ach_f = FLUX_FLOPS_PER_FACE * mesh.n_faces / (flux_t / 1e3) / 1e12
+    flux = {"bound": "alu", "kernel": "k_flux", "achieved": ach_f, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach_f / FP64_PEAK_TFLOPS, "traffic": 6617344 * mesh.n_faces / 35056,
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
+            "flops_per_face": FLUX_FLOPS_PER_FACE}
+    return dominant, flux
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="igks", choices=["igks", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="headline sweep precision (the other one is measured too)")
+    ap.add_argument("--workload", default="turbulent_plate", choices=list(WORKLOADS))
+    ap.add_argument("--ordering", default="as_given", choices=["as_given", "multicolor"],
+                    help="cell numbering = LU-SGS sweep order (the oracle baseline runs the same)")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other", action="store_true", help="skip the other precision")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    mk, fl_fn, desc = WORKLOADS[args.workload]
+    mesh, flow = mk(), fl_fn()
+    if args.ordering == "multicolor":
+        from paper_1709_00803_gb300 import igks as _ig
+        perm, ncol = _ig.order_cells(mesh, _ig.ORDER_MULTICOLOR)
+        mesh = mesh.renumbered(perm)
+        desc += f", multicolour cell order ({ncol} colours)"
+    if args.impl == "reference":
+        return run_reference(args, mesh, flow, desc)
+
+    import torch
+    dist, rank, ws = _dist()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    head = measure(args, mesh, flow, args.precision, dev, dist, ws, with_e2e=True)
+    other_p = "mixed" if args.precision == "fp64" else "fp64"
+    other = None if args.no_other else measure(args, mesh, flow, other_p, dev, dist, ws, with_e2e=False)
+    dominant, flux_roof = rooflines(head, mesh, args.precision)
+    out = {"metric": METRIC, "value": head["value"], "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if prec == igks.PREC_FP64 else "f64 flux/residual/update, f32 sweeps",
+           "dtype": "f64" if args.precision == "fp64" else "f64 flux/residual/update + f32 sweeps",
            "data": "synthetic",
            "config": {"workload": desc, "cells": mesh.n_cells, "faces": mesh.n_faces,
-                      "sweep_levels": [info["levels_fwd"], info["levels_bwd"]],
+                      "sweep_levels": [head["info"]["levels_fwd"], head["info"]["levels_bwd"]],
                       "precision": args.precision, "ordering": args.ordering,
                       "parallelism": "replicas" if ws > 1 else "single solve",
                       "l2": "flushed between steps (256 MiB write outside the timed intervals)"},
-           "e2e": e2e, "gpu_launches": ctx.launches_per_iteration() * args.steps,
-           "kernel_ms": {k: round(v, 5) for k, v in kmean.items()},
-           "roofline": roof, "clocks": clocks,
-           "solver_state": {"iters": st[sid]["iters"], "res_l2_rel": st[sid]["res_l2_rel"], "cfl": st[sid]["cfl"]}}
+           "e2e": head["e2e"], "gpu_launches": head["launches_per_step"] * args.steps,
+           "kernel_ms": head["kernel_ms"], "roofline": dominant, "roofline_flux": flux_roof,
+           "clocks": head["clocks"], "solver_state": head["solver_state"]}
+    if other:
+        out["other"] = {"precision": other_p, "value": other["value"], "ms_per_step": other["ms_per_step"],
+                        "kernel_ms": other["kernel_ms"], "clocks": other["clocks"]}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(mesh, flow, args.cpu_budget)
         out["cpu_baseline"]["cores_available"] = os.cpu_count()
     if rank == 0:
         print(json.dumps(out), flush=True)
-    ctx.destroy()
     if dist:
         dist.barrier()
         dist.destroy_process_group()

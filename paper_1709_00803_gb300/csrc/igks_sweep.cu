@@ -433,9 +433,11 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_sweep_fwd_narrow(Dev d) {
   const bool sa_on = d.flow[s].sa_on;
   const int l0 = d.lvl_solve_ptr[s], l1 = d.lvl_solve_ptr[s + 1] - 1;
   const int pbase = d.fwd_lvl[l0];
-  if (l0 < l1 && d.fwd_lvl[l0] + (int)threadIdx.x < d.fwd_lvl[l0 + 1]) fwd_stage<T>(d, d.fwd_lvl[l0] + threadIdx.x, st);
+  // level bounds travel in registers: level l spans [b, e), the next one [e, en)
+  int b = d.fwd_lvl[l0], e = d.fwd_lvl[l0 + 1];
+  if (l0 < l1 && b + (int)threadIdx.x < e) fwd_stage<T>(d, b + threadIdx.x, st);
   for (int l = l0; l < l1; l++) {
-    const int b = d.fwd_lvl[l], e = d.fwd_lvl[l + 1];
+    const int en = (l + 1 < l1) ? d.fwd_lvl[l + 2] : e;
     const bool mine = b + (int)threadIdx.x < e;
     FwdRec<T> cur;
     if (mine) {
@@ -443,7 +445,7 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_sweep_fwd_narrow(Dev d) {
       cur = *st;                 // this level's record into registers, freeing the stage
     }
     // the next level's record is in flight while this level is computed
-    if (l + 1 < l1 && e + (int)threadIdx.x < d.fwd_lvl[l + 2]) fwd_stage<T>(d, e + threadIdx.x, st);
+    if (e + (int)threadIdx.x < en) fwd_stage<T>(d, e + threadIdx.x, st);
     if (mine) fwd_process<T>(d, ring, b + threadIdx.x, pbase, &cur, sa_on);
     for (int p = b + threadIdx.x + blockDim.x; p < e; p += blockDim.x) {   // levels wider than the block
       FwdRec<T> xt;
@@ -451,6 +453,8 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_sweep_fwd_narrow(Dev d) {
       fwd_process<T>(d, ring, p, pbase, &xt, sa_on);
     }
     __syncthreads();
+    b = e;
+    e = en;
   }
 }
 
@@ -584,16 +588,17 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_sweep_bwd_narrow(Dev d) {
   const bool sa_on = d.flow[s].sa_on;
   const int l0 = d.blvl_solve_ptr[s], l1 = d.blvl_solve_ptr[s + 1] - 1;
   const int pbase = d.bwd_lvl[l0];
-  if (l0 < l1 && d.bwd_lvl[l0] + (int)threadIdx.x < d.bwd_lvl[l0 + 1]) bwd_stage<T>(d, d.bwd_lvl[l0] + threadIdx.x, st);
+  int b = d.bwd_lvl[l0], e = d.bwd_lvl[l0 + 1];
+  if (l0 < l1 && b + (int)threadIdx.x < e) bwd_stage<T>(d, b + threadIdx.x, st);
   for (int l = l0; l < l1; l++) {
-    const int b = d.bwd_lvl[l], e = d.bwd_lvl[l + 1];
+    const int en = (l + 1 < l1) ? d.bwd_lvl[l + 2] : e;
     const bool mine = b + (int)threadIdx.x < e;
     BwdRec<T> cur;
     if (mine) {
       cpa_wait_all();
       cur = *st;
     }
-    if (l + 1 < l1 && e + (int)threadIdx.x < d.bwd_lvl[l + 2]) bwd_stage<T>(d, e + threadIdx.x, st);
+    if (e + (int)threadIdx.x < en) bwd_stage<T>(d, e + threadIdx.x, st);
     if (mine) bwd_process<T>(d, ring, b + threadIdx.x, pbase, &cur, sa_on);
     for (int p = b + threadIdx.x + blockDim.x; p < e; p += blockDim.x) {   // levels wider than the block
       BwdRec<T> xt;
@@ -601,6 +606,8 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_sweep_bwd_narrow(Dev d) {
       bwd_process<T>(d, ring, p, pbase, &xt, sa_on);
     }
     __syncthreads();
+    b = e;
+    e = en;
   }
 }
 
