@@ -87,31 +87,38 @@ def build_mesh(xy: np.ndarray, cells, bc_of, name: str = "") -> Mesh:
     bc_of(a, b, xm, ym) returns the boundary tag of a boundary edge a->b with midpoint
     (xm, ym)."""
     xy = np.ascontiguousarray(xy, dtype=np.float64)
-    ptr = np.zeros(len(cells) + 1, dtype=np.int64)
-    for c, nodes in enumerate(cells):
-        ptr[c + 1] = ptr[c] + len(nodes)
+    sizes = np.fromiter((len(n) for n in cells), dtype=np.int64, count=len(cells))
+    ptr = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     flat = np.concatenate([np.asarray(n, dtype=np.int64) for n in cells]) if cells else np.zeros(0, np.int64)
-    edge_face = {}
-    fn, fc = [], []
-    for c, nodes in enumerate(cells):
-        k = len(nodes)
-        for e in range(k):
-            a, b = int(nodes[e]), int(nodes[(e + 1) % k])
-            key = (min(a, b), max(a, b))
-            f = edge_face.get(key)
-            if f is None:
-                edge_face[key] = len(fn)
-                fn.append((a, b))
-                fc.append([c, -1])
-            else:
-                if fc[f][1] != -1:
-                    raise ValueError(f"edge {key} shared by more than two cells")
-                if fn[f] != (b, a):
-                    raise ValueError(f"edge {key}: inconsistent orientation between cells")
-                fc[f][1] = c
-    face_nodes = np.asarray(fn, dtype=np.int32).reshape(-1, 2)
-    face_cells = np.asarray(fc, dtype=np.int32).reshape(-1, 2)
-    face_bc = np.zeros(face_nodes.shape[0], dtype=np.int32)
+    # directed edges a -> b of every cell, in cell order and CCW order inside a cell
+    owner = np.repeat(np.arange(len(cells), dtype=np.int64), sizes)
+    pos = np.arange(flat.shape[0], dtype=np.int64) - ptr[owner]
+    nxt = np.where(pos + 1 < sizes[owner], np.arange(flat.shape[0]) + 1, ptr[owner])
+    ea, eb = flat, flat[nxt]
+    key = np.minimum(ea, eb) * (xy.shape[0] + 1) + np.maximum(ea, eb)
+    # faces numbered by first appearance of their edge
+    uniq, first, inv, cnt = np.unique(key, return_index=True, return_inverse=True, return_counts=True)
+    if np.any(cnt > 2):
+        raise ValueError("an edge is shared by more than two cells")
+    order = np.argsort(first, kind="stable")
+    rank = np.empty_like(order)
+    rank[order] = np.arange(order.shape[0])
+    fid = rank[inv]                                   # face of every directed edge
+    nf = uniq.shape[0]
+    face_nodes = np.empty((nf, 2), dtype=np.int64)
+    face_cells = np.full((nf, 2), -1, dtype=np.int64)
+    fe = first[order]                                 # first occurrence of each face
+    face_nodes[:, 0], face_nodes[:, 1] = ea[fe], eb[fe]
+    face_cells[:, 0] = owner[fe]
+    second = np.ones(flat.shape[0], dtype=bool)
+    second[fe] = False
+    sec = np.nonzero(second)[0]
+    if np.any((ea[sec] != face_nodes[fid[sec], 1]) | (eb[sec] != face_nodes[fid[sec], 0])):
+        raise ValueError("inconsistent orientation between two cells sharing an edge")
+    face_cells[fid[sec], 1] = owner[sec]
+    face_nodes = face_nodes.astype(np.int32)
+    face_cells = face_cells.astype(np.int32)
+    face_bc = np.zeros(nf, dtype=np.int32)
     for f in range(face_nodes.shape[0]):
         if face_cells[f, 1] < 0:
             a, b = face_nodes[f]
@@ -126,14 +133,17 @@ def build_mesh(xy: np.ndarray, cells, bc_of, name: str = "") -> Mesh:
 
 def _check_ccw(m: Mesh) -> None:
     """Every cell must be a simple polygon listed counter-clockwise (signed area > 0)."""
-    x = m.xy[:, 0]
-    y = m.xy[:, 1]
-    for c in range(m.n_cells):
-        nodes = m.cell_node_list(c)
-        xs, ys = x[nodes], y[nodes]
-        a = 0.5 * np.sum(xs * np.roll(ys, -1) - np.roll(xs, -1) * ys)
-        if not a > 0.0:
-            raise ValueError(f"{m.name}: cell {c} has non-positive signed area {a}")
+    ptr = m.cell_ptr.astype(np.int64)
+    sizes = np.diff(ptr)
+    owner = np.repeat(np.arange(m.n_cells), sizes)
+    idx = np.arange(m.cell_nodes.shape[0])
+    nxt = np.where(idx + 1 < ptr[owner + 1], idx + 1, ptr[owner])
+    p, q = m.cell_nodes, m.cell_nodes[nxt]
+    cross = m.xy[p, 0] * m.xy[q, 1] - m.xy[q, 0] * m.xy[p, 1]
+    area = 0.5 * np.add.reduceat(cross, ptr[:-1]) if m.n_cells else np.zeros(0)
+    bad = np.nonzero(~(area > 0.0))[0]
+    if bad.size:
+        raise ValueError(f"{m.name}: cell {bad[0]} has non-positive signed area {area[bad[0]]}")
 
 
 # --------------------------------------------------------------------------------------
@@ -320,9 +330,24 @@ def naca_omesh(m: float = 0.0, p: float = 0.0, t: float = 0.12, n_around: int = 
     r2 = _solve_ratio(h_last * ratio, dist, n_rings)
     s = geometric_levels(h_last * ratio, r2, n_rings)
     s /= s[-1]
-    rings = [inner + sk * (far - inner) for sk in s[1:]]
+    # ring k sits at the fraction s_k of the way to the far circle, along a direction that
+    # starts as the quad layers' own extrusion direction and turns towards the far-field
+    # point (w_k = (k / n_rings)^2), so thin cells near a sharp trailing edge do not cross
+    n_in = layers[-1] - layers[-2]
+    n_in /= np.linalg.norm(n_in, axis=1, keepdims=True)
+    to_far = far - inner
+    L_far = np.linalg.norm(to_far, axis=1, keepdims=True)
+    u_far = to_far / L_far
+    rings = []
+    for k, sk in enumerate(s[1:], start=1):
+        w = (k / n_rings) ** 2
+        dvec = (1.0 - w) * n_in + w * u_far
+        dvec /= np.linalg.norm(dvec, axis=1, keepdims=True)
+        rings.append(inner + sk * L_far * dvec)
     rings[-1] = far
     # jitter interior ring points (not the quad top, not the far circle)
+    base = [r.copy() for r in rings]
+    disp = []
     for k in range(len(rings) - 1):
         prev = inner if k == 0 else rings[k - 1]
         nxt = rings[k + 1]
@@ -331,9 +356,8 @@ def naca_omesh(m: float = 0.0, p: float = 0.0, t: float = 0.12, n_around: int = 
         tangl = np.minimum(np.linalg.norm(rings[k] - np.roll(rings[k], 1, axis=0), axis=1),
                            np.linalg.norm(np.roll(rings[k], -1, axis=0) - rings[k], axis=1))
         lim = jitter * np.minimum(rad, tangl)
-        rings[k] = rings[k] + lim[:, None] * rng.uniform(-1.0, 1.0, size=(n, 2)) / math.sqrt(2.0)
-    all_layers = layers + rings
-    xy = np.concatenate(all_layers, axis=0)
+        disp.append(lim[:, None] * rng.uniform(-1.0, 1.0, size=(n, 2)) / math.sqrt(2.0))
+    disp.append(np.zeros((n, 2)))
     nid = lambda i, l: l * n + (i % n)
     cells = []
     for l in range(n_quad):
@@ -341,16 +365,44 @@ def naca_omesh(m: float = 0.0, p: float = 0.0, t: float = 0.12, n_around: int = 
             # i -> i+1 along layer l has layer l+1 on its left: CCW cell
             cells.append([nid(i, l), nid(i + 1, l), nid(i + 1, l + 1), nid(i, l + 1)])
     diag = rng.integers(0, 2, size=(n_rings, n))
+    tri = []
     for k in range(n_rings):
         l = n_quad + k
         for i in range(n):
             a, b, c, d = nid(i, l), nid(i + 1, l), nid(i + 1, l + 1), nid(i, l + 1)
             if diag[k, i] == 0:
-                cells.append([a, b, c])
-                cells.append([a, c, d])
+                tri.append([a, b, c]); tri.append([a, c, d])
             else:
-                cells.append([a, b, d])
-                cells.append([b, c, d])
+                tri.append([a, b, d]); tri.append([b, c, d])
+    tri = np.asarray(tri)
+    cells.extend(tri.tolist())
+    # thin cells near a sharp trailing edge: undo the jitter of the nodes of any triangle
+    # it inverted, and split a ring quad along its other diagonal when the chosen one
+    # inverts, until every triangle is counter-clockwise
+    n_fixed = (n_quad + 1) * n
+
+    def tri_area(xy, t):
+        P = xy[t]
+        return 0.5 * ((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1])
+                      - (P[:, 2, 0] - P[:, 0, 0]) * (P[:, 1, 1] - P[:, 0, 1]))
+    for _ in range(20):
+        xy = np.concatenate(layers + [b_ + d_ for b_, d_ in zip(base, disp)], axis=0)
+        area = tri_area(xy, tri)
+        if np.all(area > 0.0):
+            break
+        for q in np.unique(np.nonzero(area <= 0.0)[0] // 2):
+            k, i = divmod(q, n)
+            l = n_quad + k
+            a, b, c, d = nid(i, l), nid(i + 1, l), nid(i + 1, l + 1), nid(i, l + 1)
+            alt = np.array([[a, b, d], [b, c, d]]) if diag[k, i] == 0 else np.array([[a, b, c], [a, c, d]])
+            if np.all(tri_area(xy, alt) > 0.0):
+                diag[k, i] = 1 - diag[k, i]
+                tri[2 * q:2 * q + 2] = alt
+            else:
+                for g in {a, b, c, d}:
+                    if g >= n_fixed:
+                        disp[(g - n_fixed) // n][(g - n_fixed) % n] = 0.0
+    cells = cells[:n_quad * n] + tri.tolist()
     wall_nodes = n  # nodes 0..n-1 are on the body
 
     def bc(a, b, xm, ym):
@@ -441,3 +493,35 @@ def turbulent_plate(seed: int = 1) -> Mesh:
 def naca0012(seed: int = 3) -> Mesh:
     """NACA 0012 hybrid O-mesh, 320 x 48 quads + 320 x 70 x 2 triangles (60160 cells)."""
     return naca_omesh(0.0, 0.0, 0.12, seed=seed, name="naca0012_60160")
+
+
+def naca_scaled(m: float, p: float, t: float, target_cells: int, seed: int, name: str = "") -> Mesh:
+    """A NACA 4-digit O-mesh built like the NACA 0012 workload with its point and layer
+    counts scaled by sqrt(target_cells / 60160) (cells = n_around (n_quad + 2 n_rings))."""
+    s = math.sqrt(target_cells / 60160.0)
+    n_around = max(64, 2 * int(round(160 * s)))
+    n_quad = max(12, int(round(48 * s)))
+    n_rings = max(8, int(round(70 * s)))
+    # keep the quad layer as thick as the full-size one (first spacing 1e-6, 48 layers,
+    # ratio 1.2): the growth ratio follows from the layer count
+    height = geometric_levels(1e-6, 1.2, 48)[-1]
+    ratio = _solve_ratio(1e-6, height, n_quad)
+    return naca_omesh(m, p, t, n_around=n_around, n_quad=n_quad, ratio=ratio, n_rings=n_rings, seed=seed,
+                      name=name or f"naca{m:.3f}_{p:.2f}_{t:.2f}_{n_around}x{n_quad}+{n_rings}")
+
+
+def naca_batch_specs(n: int = 64, seed: int = 4, cells_lo: int = 8000, cells_hi: int = 80000):
+    """Seeded parameters of the batched-airfoil workload: per case the NACA 4-digit shape
+    (m in [0, 0.06], p in [0.2, 0.6], t in [0.08, 0.18]), the flow (Ma in [0.1, 0.75],
+    AoA in [-4, 8] deg, Re_c log-uniform in [1e6, 1e7]) and a target cell count drawn
+    log-uniform in [cells_lo, cells_hi]. Case i uses seed 1000 * seed + i for its mesh."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(n):
+        specs.append(dict(
+            m=float(rng.uniform(0.0, 0.06)), p=float(rng.uniform(0.2, 0.6)), t=float(rng.uniform(0.08, 0.18)),
+            mach=float(rng.uniform(0.1, 0.75)), aoa=float(rng.uniform(-4.0, 8.0)),
+            reynolds=float(10 ** rng.uniform(6.0, 7.0)),
+            cells=int(round(10 ** rng.uniform(math.log10(cells_lo), math.log10(cells_hi)))),
+            mesh_seed=1000 * seed + i))
+    return specs
