@@ -195,6 +195,22 @@ int igks_mesh_info(igks_ctx* ctx, int32_t solve, int32_t* out /*[5]*/);
  * coefficients about the free-stream direction: out[0] Cl, out[1] Cd, out[2] Cd_viscous. */
 int igks_get_forces(igks_ctx* ctx, int32_t solve, int32_t bc_tag, double* out /*[3]*/);
 
+/* Launch configuration chosen by igks_autotune. */
+typedef struct igks_tuning {
+  int32_t sweep_threads;   /* threads per block of the one-block-per-solve sweeps */
+  int32_t flux_block;      /* threads per block of the flux kernel */
+  int32_t sweep_mode;      /* 1 one block per solve, 2 one launch per level */
+  float ms_per_iter;       /* measured device time of one iteration with it */
+} igks_tuning;
+
+/* Time the library's launch configurations (sweep schedule and block size, flux block
+ * size) on the context's live solves, iters_per_trial iterations each after one warm-up
+ * iteration, and keep the fastest. Every trial starts from the same saved state and the
+ * state is restored afterwards: the configurations do not change the arithmetic, so the
+ * solves' iterates are exactly those of an untuned run. Allocates temporary device
+ * memory. out (nullable) receives the choice. Errors: IGKS_EINVAL, IGKS_ECUDA. */
+int igks_autotune(igks_ctx* ctx, int32_t iters_per_trial, igks_tuning* out);
+
 /* Number of kernel launches one iteration issues (for launch accounting). */
 int igks_launches_per_iteration(igks_ctx* ctx, int32_t* out);
 

@@ -886,6 +886,94 @@ int igks_order_cells(int32_t n_cells, int32_t n_faces, const int32_t* face_cells
   return IGKS_OK;
 }
 
+// re-capture the iteration graph after a launch parameter changed
+static int recapture(igks_ctx* ctx) {
+  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+  if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+  if (!ctx->opt.use_graph) return 0;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_iteration(ctx);
+  CK(cudaStreamEndCapture(ctx->stream, &ctx->graph));
+  CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
+  return 0;
+}
+
+int igks_autotune(igks_ctx* ctx, int32_t iters_per_trial, igks_tuning* out) {
+  if (!ctx || iters_per_trial <= 0) return IGKS_EINVAL;
+  int rc = build(ctx);
+  if (rc) return rc;
+  Dev& d = ctx->dev;
+  const int ns = d.n_solves;
+  // the state every trial starts from (per-cell fields and per-solve iteration state)
+  double* Wb = nullptr;
+  SolveState* Sb = nullptr;
+  unsigned long long* Tb = nullptr;
+  const size_t wbytes = sizeof(double) * 5 * (size_t)ctx->nc_pad;
+  CK(cudaMalloc(&Wb, wbytes));
+  CK(cudaMalloc(&Sb, sizeof(SolveState) * ns));
+  CK(cudaMalloc(&Tb, sizeof(unsigned long long) * ns));
+  auto save = [&]() {
+    cudaMemcpyAsync(Wb, d.W, wbytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaMemcpyAsync(Sb, d.st, sizeof(SolveState) * ns, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaMemcpyAsync(Tb, d.dt_bits, sizeof(unsigned long long) * ns, cudaMemcpyDeviceToDevice, ctx->stream);
+  };
+  auto restore = [&]() {
+    cudaMemcpyAsync(d.W, Wb, wbytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaMemcpyAsync(d.st, Sb, sizeof(SolveState) * ns, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaMemcpyAsync(d.dt_bits, Tb, sizeof(unsigned long long) * ns, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaMemsetAsync(d.eq40_bits, 0, sizeof(unsigned long long) * ns, ctx->stream);
+    cudaMemsetAsync(d.bad, 0, sizeof(int) * ns, ctx->stream);
+  };
+  save();
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  igks_tuning best{};
+  best.ms_per_iter = 1e30f;
+  const bool wide_ok = std::max(d.n_wfwd, d.n_wbwd) <= 4 * WIDE_MAX_LEVELS;
+  const int flux_blocks[] = {64, 128};
+  const int sweep_threads[] = {128, 256};
+  int err = 0;
+  for (int wide = 0; wide <= (wide_ok ? 1 : 0) && !err; wide++)
+    for (int fb : flux_blocks)
+      for (int stt : sweep_threads) {
+        if (wide && stt != sweep_threads[0]) continue;   // the wide schedule has its own block
+        d.wide = wide;
+        d.flux_block = fb;
+        ctx->opt.sweep_threads = stt;
+        if ((err = recapture(ctx))) break;
+        restore();
+        for (int r = 0; r <= iters_per_trial; r++) {
+          if (r == 1) cudaEventRecord(e0, ctx->stream);   // the first iteration warms up
+          if (ctx->gexec) cudaGraphLaunch(ctx->gexec, ctx->stream);
+          else enqueue_iteration(ctx);
+        }
+        cudaEventRecord(e1, ctx->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { err = IGKS_ECUDA; break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= iters_per_trial;
+        if (ms < best.ms_per_iter) best = igks_tuning{stt, fb, wide ? 2 : 1, ms};
+      }
+  // apply the winner and put every solve back where it was
+  d.wide = best.sweep_mode == 2;
+  d.flux_block = best.flux_block;
+  ctx->opt.sweep_threads = best.sweep_threads;
+  ctx->opt.sweep_mode = best.sweep_mode;
+  if (!err) err = recapture(ctx);
+  restore();
+  cudaStreamSynchronize(ctx->stream);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(Wb);
+  cudaFree(Sb);
+  cudaFree(Tb);
+  CK(cudaGetLastError());
+  if (err) return fail(ctx, err, "autotune trial failed");
+  if (out) *out = best;
+  return IGKS_OK;
+}
+
 int igks_launches_per_iteration(igks_ctx* ctx, int32_t* out) {
   if (!ctx || !out) return IGKS_EINVAL;
   int rc = build(ctx);

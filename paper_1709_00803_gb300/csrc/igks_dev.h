@@ -122,6 +122,7 @@ struct Dev {
   int* bad;                      // [n_solves] divergence flag of the current update
   double* part;                  // [2][n_blocks] residual norm partials per cell block
   int n_cell_blocks;
+  int flux_block;                // threads per block of the flux kernel (<= 128)
   int* err;                      // [4] device error flags (mesh orientation, area)
 };
 

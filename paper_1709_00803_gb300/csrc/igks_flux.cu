@@ -338,7 +338,8 @@ __global__ void __launch_bounds__(128) k_flux(Dev d) {
 }
 
 void launch_flux(const Dev& d, cudaStream_t s) {
-  if (d.nf) k_flux<<<(d.nf + 127) / 128, 128, 0, s>>>(d);
+  const int b = d.flux_block > 0 ? d.flux_block : 128;
+  if (d.nf) k_flux<<<(d.nf + b - 1) / b, b, 0, s>>>(d);
 }
 
 }  // namespace igks

@@ -39,6 +39,11 @@ class Flow(C.Structure):
                 ("c_num", C.c_double), ("visc_sr", C.c_int32), ("pad_", C.c_int32)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("sweep_threads", C.c_int32), ("flux_block", C.c_int32), ("sweep_mode", C.c_int32),
+                ("ms_per_iter", C.c_float)]
+
+
 class Status(C.Structure):
     _fields_ = [("iters", C.c_int32), ("state", C.c_int32), ("res_l2_rho", C.c_double),
                 ("res_l2_rel", C.c_double), ("res_inf", C.c_double), ("eq40_ratio", C.c_double),
@@ -81,6 +86,8 @@ def lib():
         L.igks_kernel_name.restype = C.c_char_p
         L.igks_residual_norms_noalloc.argtypes = [vp, vp, i32, vp, vp]
         L.igks_residual_norms_noalloc.restype = C.c_int32
+        L.igks_autotune.argtypes = [vp, i32, P(Tuning)]
+        L.igks_autotune.restype = C.c_int32
         L.igks_order_cells.argtypes = [i32, i32, ip, i32, ip, ip]
         L.igks_order_cells.restype = C.c_int32
         for name in ("igks_create", "igks_mesh_upload", "igks_set_flow", "igks_init_freestream",
@@ -190,6 +197,11 @@ class Context:
 
     def enqueue(self, n_iters):
         self._check(lib().igks_enqueue(self.h, n_iters))
+
+    def autotune(self, iters_per_trial=3):
+        t = Tuning()
+        self._check(lib().igks_autotune(self.h, iters_per_trial, C.byref(t)))
+        return {k: getattr(t, k) for k, _ in t._fields_}
 
     def kernel_times(self):
         ms = (C.c_float * 32)()

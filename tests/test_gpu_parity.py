@@ -211,3 +211,25 @@ def test_forced_wide_schedule_on_deep_ordering():
     ctx2, sid2, ora2 = make_pair(m, fl, seeded(m, fl, 13), sweep_mode=1, precision=1)
     ctx2.iterate(1); ora2.iterate(1)
     assert_close("dw fp32 narrow", ctx2.get_array(sid2, "dw")[:4], ora2.get(O.ORA_DW)[:4], 2e-5)
+
+
+def test_autotune_leaves_iterates_unchanged():
+    from paper_1709_00803_gb300 import igks
+    cases = [(G.flat_plate_hybrid(nx=48, nq=16, ntri_rows=12, first=1e-5, seed=3), F.turbulent_plate_flow()),
+             (G.laminar_plate(), F.laminar_plate_flow())]
+    results = []
+    for tune in (False, True):
+        ctx = igks.Context(precision=1)
+        for m, fl in cases:
+            sid = ctx.mesh_upload(m); ctx.set_flow(sid, fl)
+        for k in range(len(cases)):
+            ctx.init_freestream(k)
+        ctx.iterate(5)
+        if tune:
+            choice = ctx.autotune(2)
+            assert choice["sweep_mode"] in (1, 2) and choice["ms_per_iter"] > 0
+        ctx.iterate(10)
+        results.append([ctx.get_fields(k) for k in range(len(cases))])
+        ctx.destroy()
+    for a, b in zip(*results):
+        assert np.array_equal(a, b)
