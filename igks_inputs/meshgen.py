@@ -31,7 +31,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-BC_INTERIOR, BC_FARFIELD, BC_SYMMETRY, BC_WALL = 0, 1, 2, 3
+BC_INTERIOR, BC_FARFIELD, BC_SYMMETRY, BC_WALL, BC_OUTFLOW = 0, 1, 2, 3, 4
 
 
 @dataclass
@@ -178,10 +178,12 @@ def _solve_ratio(first: float, total: float, n: int) -> float:
 def _plate_bc(x0_wall: float = 0.0, xmin: float = -0.5, xmax: float = 1.0, ymax: float = 1.0):
     tol = 1e-12
 
+    # as the paper's flat plates: free stream at the inflow (left) boundary, the
+    # Riemann-invariant outflow condition on the upper and outflow boundaries
     def bc(a, b, xm, ym):
         if abs(ym) < tol:
             return BC_WALL if xm >= x0_wall else BC_SYMMETRY
-        return BC_FARFIELD
+        return BC_FARFIELD if abs(xm - xmin) < tol else BC_OUTFLOW
     return bc
 
 
@@ -208,7 +210,7 @@ def flat_plate_quads(nx: int = 64, ny: int = 32, ratio: float = 1.1,
     for j in range(ny):
         for i in range(nx):
             cells.append([nid(i, j), nid(i + 1, j), nid(i + 1, j + 1), nid(i, j + 1)])
-    m = build_mesh(xy, cells, _plate_bc(), name=name)
+    m = build_mesh(xy, cells, _plate_bc(xmin=xmin), name=name)
     m.meta = dict(kind="plate", nx=nx, ny=ny, first=float(first), ratio=float(ratio))
     return m
 
@@ -262,7 +264,7 @@ def flat_plate_hybrid(nx: int = 128, nq: int = 64, ntri_rows: int = 48, first: f
             else:                  # split along b-d
                 cells.append([a, b, d])
                 cells.append([b, c, d])
-    m = build_mesh(xy, cells, _plate_bc(), name=name)
+    m = build_mesh(xy, cells, _plate_bc(xmin=xmin), name=name)
     m.meta = dict(kind="plate_hybrid", nx=nx, nq=nq, ntri_rows=ntri_rows, first=first,
                   ratio=ratio, seed=seed)
     return m
@@ -275,10 +277,12 @@ def flat_plate_hybrid(nx: int = 128, nq: int = 64, ntri_rows: int = 48, first: f
 def naca4_surface(m: float, p: float, t: float, n_around: int) -> np.ndarray:
     """Closed-trailing-edge NACA 4-digit section, n_around points starting at the
     trailing edge, along the lower surface to the leading edge and back along the upper
-    surface (clockwise around the body; cosine clustering)."""
+    surface (clockwise around the body; half-cosine clustering)."""
     half = n_around // 2
     beta = np.linspace(0.0, math.pi, half + 1)
-    xc = 0.5 * (1.0 - np.cos(beta))  # 0 (LE) .. 1 (TE)
+    # half cosine, half uniform: points gather towards the edges without making the
+    # first triangle rings above the quad layers needle-shaped there
+    xc = 0.25 * (1.0 - np.cos(beta)) + 0.5 * beta / math.pi  # 0 (LE) .. 1 (TE)
     yt = 5.0 * t * (0.2969 * np.sqrt(xc) - 0.1260 * xc - 0.3516 * xc ** 2
                     + 0.2843 * xc ** 3 - 0.1036 * xc ** 4)
     if m > 0.0 and p > 0.0:
@@ -299,14 +303,59 @@ def naca4_surface(m: float, p: float, t: float, n_around: int) -> np.ndarray:
     return pts[:n_around]
 
 
+def _march_rings(inner: np.ndarray, h0: float, n_rings: int, r_far: float, centre: np.ndarray):
+    """Rings of an O-grid from the closed curve `inner` (clockwise, fluid on the left of
+    its tangent) out to the circle of radius r_far about `centre`: each ring steps from
+    the previous one along its smoothed left normal, by steps growing geometrically from
+    h0, and is then smoothed along itself (which rounds it and evens out its spacing);
+    over the outer third the rings are blended onto circles, the last one onto the far
+    circle. Marching normals of a rounding curve do not cross, so no cell folds."""
+    n = inner.shape[0]
+    d_far = r_far - np.linalg.norm(inner - centre, axis=1).mean()
+    q = _solve_ratio(h0, d_far, n_rings)
+    steps = h0 * q ** np.arange(n_rings)
+    rings, X = [], inner.copy()
+    k_blend = int(round(0.65 * n_rings))
+    for k in range(n_rings):
+        t = np.roll(X, -1, axis=0) - np.roll(X, 1, axis=0)
+        nrm = np.stack([-t[:, 1], t[:, 0]], axis=1)
+        nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+        for _ in range(2 + k // 4):
+            nrm = nrm + 0.5 * (np.roll(nrm, 1, axis=0) + np.roll(nrm, -1, axis=0))
+            nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+        X = X + steps[k] * nrm
+        nu = min(0.5, 0.05 + 0.45 * k / n_rings)
+        for _ in range(2):
+            X = X + nu * (0.5 * (np.roll(X, 1, axis=0) + np.roll(X, -1, axis=0)) - X)
+        # move the points along the ring towards even arc-length spacing (fully even from
+        # 60% of the rings out), keeping point 0 in place: far from the body the cells
+        # then have the same aspect ratio all around
+        w = min(1.0, (k + 1) / (0.6 * n_rings))
+        seg = np.linalg.norm(np.roll(X, -1, axis=0) - X, axis=1)
+        s_pts = np.concatenate([[0.0], np.cumsum(seg)])
+        L = s_pts[-1]
+        target = (1.0 - w) * s_pts[:-1] + w * L * np.arange(n) / n
+        Xc = np.concatenate([X, X[:1]], axis=0)
+        X = np.stack([np.interp(target, s_pts, Xc[:, 0]), np.interp(target, s_pts, Xc[:, 1])], axis=1)
+        if k >= k_blend:
+            rel = X - centre
+            rad = np.linalg.norm(rel, axis=1, keepdims=True)
+            r_k = r_far if k == n_rings - 1 else rad.mean()
+            w = 1.0 if k == n_rings - 1 else (k - k_blend + 1) / (n_rings - k_blend)
+            X = (1.0 - w) * X + w * (centre + r_k * rel / rad)
+        rings.append(X.copy())
+    return rings
+
+
 def naca_omesh(m: float = 0.0, p: float = 0.0, t: float = 0.12, n_around: int = 320,
                n_quad: int = 48, first: float = 1e-6, ratio: float = 1.2,
                n_rings: int = 70, r_far: float = 20.0, jitter: float = 0.25,
                seed: int = 3, name: str = "naca_omesh") -> Mesh:
     """Hybrid O-mesh around a NACA 4-digit section: n_around x n_quad body-fitted quad
-    layers (first spacing `first`, growth `ratio`), then n_rings rings out to a circle of
-    radius r_far centred at (0.5, 0), the ring cells split into seeded-random triangles
-    and interior ring points jittered by up to +-jitter of the local spacing."""
+    layers (first spacing `first`, growth `ratio`), then n_rings rings marched out to a
+    circle of radius r_far centred at (0.5, 0) (see _march_rings), the ring cells split
+    into seeded-random triangles and interior ring points jittered by up to +-jitter of
+    the local spacing."""
     rng = np.random.default_rng(seed)
     surf = naca4_surface(m, p, t, n_around)
     n = surf.shape[0]
@@ -316,35 +365,22 @@ def naca_omesh(m: float = 0.0, p: float = 0.0, t: float = 0.12, n_around: int = 
     tang /= np.linalg.norm(tang, axis=1, keepdims=True)
     nrm = np.stack([-tang[:, 1], tang[:, 0]], axis=1)
     offs = geometric_levels(first, ratio, n_quad)
-    layers = [surf + o * nrm for o in offs]
+    # extrusion directions: the wall normal at the wall, turning with height towards a
+    # smoothed normal, so that the fan around the sharp trailing edge spreads over many
+    # cells of the upper layers instead of one
+    smooth = nrm.copy()
+    for _ in range(max(8, n // 4)):
+        smooth = smooth + 0.5 * (np.roll(smooth, 1, axis=0) + np.roll(smooth, -1, axis=0))
+        smooth /= np.linalg.norm(smooth, axis=1, keepdims=True)
+    layers = [surf.copy()]
+    for l in range(1, len(offs)):
+        w = offs[l] / offs[-1]
+        dvec = (1.0 - w) * nrm + w * smooth
+        dvec /= np.linalg.norm(dvec, axis=1, keepdims=True)
+        layers.append(layers[-1] + (offs[l] - offs[l - 1]) * dvec)
     inner = layers[-1]
     h_last = offs[-1] - offs[-2]
-    # ring blend parameter from the quad top to the far circle
-    ang = np.zeros(n)
-    # far-field angles follow the surface parameter: TE at angle 0, LE at pi
-    half = n // 2
-    ang[:half + 1] = -np.linspace(0.0, math.pi, half + 1)        # lower: 0 .. -pi
-    ang[half + 1:] = np.linspace(math.pi, 0.0, n - half + 1)[1:-1]  # upper: pi .. 0
-    far = np.stack([0.5 + r_far * np.cos(ang), r_far * np.sin(ang)], axis=1)
-    dist = np.linalg.norm(far - inner, axis=1).mean()
-    r2 = _solve_ratio(h_last * ratio, dist, n_rings)
-    s = geometric_levels(h_last * ratio, r2, n_rings)
-    s /= s[-1]
-    # ring k sits at the fraction s_k of the way to the far circle, along a direction that
-    # starts as the quad layers' own extrusion direction and turns towards the far-field
-    # point (w_k = (k / n_rings)^2), so thin cells near a sharp trailing edge do not cross
-    n_in = layers[-1] - layers[-2]
-    n_in /= np.linalg.norm(n_in, axis=1, keepdims=True)
-    to_far = far - inner
-    L_far = np.linalg.norm(to_far, axis=1, keepdims=True)
-    u_far = to_far / L_far
-    rings = []
-    for k, sk in enumerate(s[1:], start=1):
-        w = (k / n_rings) ** 2
-        dvec = (1.0 - w) * n_in + w * u_far
-        dvec /= np.linalg.norm(dvec, axis=1, keepdims=True)
-        rings.append(inner + sk * L_far * dvec)
-    rings[-1] = far
+    rings = _march_rings(inner, h_last * ratio, n_rings, r_far, np.array([0.5, 0.0]))
     # jitter interior ring points (not the quad top, not the far circle)
     base = [r.copy() for r in rings]
     disp = []
@@ -437,8 +473,8 @@ def tiny_quads(nx: int = 2, ny: int = 2, skew: float = 0.0, seed: int = 0,
     nid = lambda i, j: j * (nx + 1) + i
     cells = [[nid(i, j), nid(i + 1, j), nid(i + 1, j + 1), nid(i, j + 1)]
              for j in range(ny) for i in range(nx)]
-    bottom = {"wall": BC_WALL, "symmetry": BC_SYMMETRY, "farfield": BC_FARFIELD}[bcs[0]]
-    other = {"wall": BC_WALL, "symmetry": BC_SYMMETRY, "farfield": BC_FARFIELD}[bcs[1]]
+    tags = {"wall": BC_WALL, "symmetry": BC_SYMMETRY, "farfield": BC_FARFIELD, "outflow": BC_OUTFLOW}
+    bottom, other = tags[bcs[0]], tags[bcs[1]]
     return build_mesh(xy, cells, lambda a, b, xm, ym: bottom if abs(ym) < 1e-12 else other,
                       name=f"tiny_quads_{nx}x{ny}")
 
@@ -453,8 +489,8 @@ def triangle_fan(n: int = 4, radius: float = 1.0) -> Mesh:
 
 def mixed_polygons(seed: int = 0) -> Mesh:
     """A small mesh mixing a quad row, a pentagon, a hexagon and triangles: the
-    general-polygon cells the hybrid meshes of the paper contain. Bottom is wall,
-    the rest far field."""
+    general-polygon cells the hybrid meshes of the paper contain. Bottom is wall, the
+    right side outflow, the rest free stream."""
     xy = np.array([
         [0.0, 0.0], [1.0, 0.0], [2.0, 0.0], [3.0, 0.0],      # 0..3 bottom
         [0.0, 1.0], [1.0, 1.0], [2.0, 1.0], [3.0, 1.0],      # 4..7
@@ -472,8 +508,8 @@ def mixed_polygons(seed: int = 0) -> Mesh:
         [8, 6, 13, 11],          # quad
         [13, 12, 11],            # triangle
     ]
-    return build_mesh(xy, cells, lambda a, b, xm, ym: BC_WALL if abs(ym) < 1e-12 else BC_FARFIELD,
-                      name="mixed_polygons")
+    return build_mesh(xy, cells, lambda a, b, xm, ym: BC_WALL if abs(ym) < 1e-12 else
+                      (BC_OUTFLOW if abs(xm - 3.0) < 1e-12 else BC_FARFIELD), name="mixed_polygons")
 
 
 # --------------------------------------------------------------------------------------

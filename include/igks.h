@@ -45,9 +45,11 @@ extern "C" {
 
 /* boundary tags of face_bc (Section II.E) */
 #define IGKS_BC_INTERIOR 0
-#define IGKS_BC_FARFIELD 1  /* characteristic (Riemann-invariant) far field */
+#define IGKS_BC_FARFIELD 1  /* free stream: the ghost cell holds the free-stream state */
 #define IGKS_BC_SYMMETRY 2
 #define IGKS_BC_WALL 3      /* adiabatic non-slip wall */
+#define IGKS_BC_OUTFLOW 4   /* outflow: boundary-normal velocity from the Riemann invariants,
+                               density, tangential velocity, temperature and nu_tilde from inside */
 
 /* precision of the LU-SGS sweeps; flux, residual and state update are always FP64 */
 #define IGKS_PREC_FP64 0
@@ -256,6 +258,112 @@ int igks_residual_norms_noalloc(const double* m_rho, const double* area, int32_t
 
 /* Message of the last error on this context (owned by the context; never NULL). */
 const char* igks_last_error(igks_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------
+ * Device memory accounting.
+ * igks_footprint_bytes: upper bound of the device bytes one solve of this size takes in
+ * a context (host only; nnz = cell_ptr[n_cells], the summed face count of the cells).
+ * igks_device_bytes: device bytes the context holds now (0 before the first build). */
+int igks_footprint_bytes(int32_t n_nodes, int32_t n_cells, int32_t n_faces, int32_t nnz, int64_t* out);
+int igks_device_bytes(igks_ctx* ctx, int64_t* out);
+
+/* ---------------------------------------------------------------------------------
+ * Serving: continuous batching of steady solves (the paper solves one case at a time;
+ * this layer has no counterpart there and adds no arithmetic: every solve runs the same
+ * iteration as a context of its own and ends with bitwise the same fields).
+ *
+ * A server owns a FIFO queue of submitted requests and a set of resident cohorts. A
+ * cohort is a context holding the solves admitted together, on its own CUDA stream, so
+ * that the cohorts' iterations overlap on the GPU. igks_server_step
+ *   1. retires the solves that stopped (converged, diverged or at the iteration cap):
+ *      records the finish time, Cl/Cd/c on IGKS_BC_WALL faces and (keep_fields) the
+ *      fields, and destroys a cohort once none of its solves is live;
+ *   2. admits queued requests in arrival order while a slot is free (live solves <
+ *      max_slots) and the HBM budget holds their igks_footprint_bytes, into one new
+ *      cohort; cohorts whose live cells fell below repack_fraction of their cells move
+ *      their live solves (fields and iteration state, bitwise) into that cohort too and
+ *      are freed, so finished solves stop holding memory;
+ *   3. enqueues iters_per_step iterations on every cohort with live solves, then waits
+ *      for all of them. Solves stop on the device at their own iteration (a converged
+ *      solve is skipped by every kernel), so a step never runs a solve past its stop.
+ * Times are seconds of a steady host clock since igks_server_create. */
+#define IGKS_MAXITER (-8)   /* result state: stopped at max_iters without converging */
+
+typedef struct igks_server_options {
+  int32_t precision;        /* IGKS_PREC_* of every solve */
+  int32_t device;           /* CUDA device ordinal */
+  int32_t max_slots;        /* live solves at most (>= 1) */
+  int32_t max_cohort;       /* requests admitted into one new cohort at most (>= 1) */
+  int32_t iters_per_step;   /* iterations per igks_server_step (>= 1) */
+  int32_t max_iters;        /* iteration cap of a solve (>= 1) */
+  int64_t hbm_budget;       /* device bytes the resident cohorts may hold; 0: 90% of the
+                               free device memory at creation */
+  double repack_fraction;   /* see step 2; 0 disables repacking */
+  int32_t keep_fields;      /* keep the fields of finished solves for igks_server_take_fields */
+  int32_t reserved[7];
+} igks_server_options;
+
+typedef struct igks_request {
+  /* mesh, as for igks_mesh_upload (copied at submit) */
+  int32_t n_nodes;
+  const double* xy;
+  int32_t n_cells;
+  const int32_t* cell_ptr;
+  const int32_t* cell_nodes;
+  int32_t n_faces;
+  const int32_t* face_nodes;
+  const int32_t* face_cells;
+  const int32_t* face_bc;
+  igks_flow flow;
+  int64_t tag;              /* caller's value, returned in the result */
+} igks_request;
+
+typedef struct igks_result {
+  int64_t id, tag;
+  int32_t state;            /* IGKS_CONVERGED, IGKS_DIVERGED or IGKS_MAXITER */
+  int32_t iters;
+  int32_t n_cells;
+  int32_t cohort;           /* serial number of the cohort the solve finished in */
+  double res_l2_rel;        /* final RMS(M_rho / Omega) over its first-iteration value */
+  double t_submit, t_admit, t_finish;
+  double forces[3];         /* igks_get_forces on IGKS_BC_WALL faces at the finish */
+  int64_t footprint;        /* igks_footprint_bytes of the solve */
+} igks_result;
+
+typedef struct igks_server_status {
+  int32_t queued;           /* submitted, not admitted */
+  int32_t live;             /* admitted, still iterating */
+  int32_t cohorts;          /* resident contexts */
+  int32_t finished;         /* results waiting for igks_server_poll */
+  int64_t bytes;            /* footprint of the resident cohorts */
+  int64_t budget;           /* the HBM budget in force */
+  int32_t admitted;         /* requests admitted by the last step */
+  int32_t repacked;         /* live solves moved between cohorts by the last step */
+  double step_s;            /* wall time of the last step */
+} igks_server_status;
+
+typedef struct igks_server igks_server;
+
+/* Errors: IGKS_EINVAL (bad option), IGKS_ECUDA. */
+int igks_server_create(const igks_server_options* opt, igks_server** out);
+/* Queue one request; *id receives its id (ids count up from 0). The mesh is validated
+ * here (IGKS_EMESH) and the flow too (IGKS_EINVAL). A request whose footprint exceeds
+ * the whole budget is refused with IGKS_ENOMEM. */
+int igks_server_submit(igks_server* srv, const igks_request* req, int64_t* id);
+/* One retire/admit/run round as described above. status (nullable) describes the
+ * server after the step. Errors: IGKS_ECUDA, IGKS_ENOMEM (a cohort could not be
+ * built: its requests go back to the queue head). */
+int igks_server_step(igks_server* srv, igks_server_status* status);
+/* Move up to cap finished results, in finish order, to out; *n receives the count. */
+int igks_server_poll(igks_server* srv, igks_result* out, int32_t cap, int32_t* n);
+/* Copy the fields ([5][n_cells] SoA, as igks_get_fields) of a finished solve and free
+ * the server's copy. IGKS_EINVAL if the id has no kept fields. */
+int igks_server_take_fields(igks_server* srv, int64_t id, double* W);
+/* Seconds on the server clock. */
+int igks_server_now(igks_server* srv, double* t);
+int igks_server_get_status(igks_server* srv, igks_server_status* status);
+int igks_server_destroy(igks_server* srv);
+const char* igks_server_last_error(igks_server* srv);
 
 #ifdef __cplusplus
 }

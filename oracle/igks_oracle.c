@@ -656,31 +656,28 @@ static void ghost_state(const ora_solver* s, int f, const double* Wi, double* Wg
   } else if (bc == 2) {         /* symmetry: normal momentum changes sign */
     double mn = Wi[1] * nx + Wi[2] * ny;
     Wg[0] = Wi[0]; Wg[1] = Wi[1] - 2.0 * mn * nx; Wg[2] = Wi[2] - 2.0 * mn * ny; Wg[3] = Wi[3]; Wg[4] = Wi[4];
-  } else {                      /* far field: Riemann invariants normal to the face */
+  } else if (bc == 4) {         /* outflow (Section II.E): the boundary-normal velocity is half the
+                                   sum of the Riemann invariants R+ (inside) and R- (free stream);
+                                   density, tangential velocity, temperature (lambda) and nu_tilde
+                                   are the inside values */
     double Wf[5];
     freestream(&s->flow, Wf);
     double g = GAMMA;
-    double ri = Wi[0], ui = Wi[1] / ri, vi = Wi[2] / ri, pi = pressure(Wi), ci = sqrt(g * pi / ri);
-    double ro = Wf[0], uo = Wf[1] / ro, vo = Wf[2] / ro, po = pressure(Wf), co = sqrt(g * po / ro);
-    double uni = ui * nx + vi * ny, uno = uo * nx + vo * ny;
-    if (uni <= -ci) { memcpy(Wg, Wf, sizeof(double) * 5); return; }
-    if (uni >= ci) { memcpy(Wg, Wi, sizeof(double) * 5); return; }
+    double ri = Wi[0], ui = Wi[1] / ri, vi = Wi[2] / ri, ci = sqrt(g * pressure(Wi) / ri);
+    double co = sqrt(g * pressure(Wf) / Wf[0]);
+    double uni = ui * nx + vi * ny, uno = (Wf[1] * nx + Wf[2] * ny) / Wf[0];
     double Rp = uni + 2.0 * ci / (g - 1.0);
     double Rm = uno - 2.0 * co / (g - 1.0);
     double ub = 0.5 * (Rp + Rm);
-    double cb = 0.25 * (g - 1.0) * (Rp - Rm);
-    double ut, vt, ent, nut;
-    if (ub > 0.0) {             /* outflow: tangential velocity, entropy and nu_tilde from inside */
-      ut = ui - uni * nx; vt = vi - uni * ny; ent = pi / pow(ri, g); nut = Wi[4];
-    } else {                    /* inflow: from the free stream */
-      ut = uo - uno * nx; vt = vo - uno * ny; ent = po / pow(ro, g); nut = Wf[4];
-    }
-    double rb = pow(cb * cb / (g * ent), 1.0 / (g - 1.0));
-    double pb = rb * cb * cb / g;
-    double ubx = ub * nx + ut, uby = ub * ny + vt;
-    Wg[0] = rb; Wg[1] = rb * ubx; Wg[2] = rb * uby;
-    Wg[3] = pb / (g - 1.0) + 0.5 * rb * (ubx * ubx + uby * uby);
-    Wg[4] = nut;
+    double ut = ui - uni * nx, vt = vi - uni * ny;          /* tangential velocity, inside */
+    double lam_i = (KDOF + 2.0) * ri / (4.0 * (Wi[3] - 0.5 * ri * (ui * ui + vi * vi)));
+    double rb = ri;
+    double bx = ub * nx + ut, by = ub * ny + vt;
+    Wg[0] = rb; Wg[1] = rb * bx; Wg[2] = rb * by;
+    Wg[3] = 0.5 * rb * (ub * ub + (ut * ut + vt * vt) + (KDOF + 2.0) / (2.0 * lam_i));
+    Wg[4] = Wi[4];
+  } else {                      /* free stream (Section II.E): the ghost holds the free stream */
+    freestream(&s->flow, Wg);
   }
 }
 
@@ -860,7 +857,7 @@ static int step_fluxes(ora_solver* s) {
       face_bc_map(bc, SLt, SRt);
       dR = dL;
     } else {
-      /* far field: the ghost holds a constant state */
+      /* free stream and outflow: the ghost state, without slopes */
       for (int v = 0; v < 4; v++) { WR[v] = WcR[v]; SRn[v] = 0.0; SRt[v] = 0.0; }
       dR = dL;
     }
@@ -1043,7 +1040,7 @@ static void step_sweeps(ora_solver* s) {
       double dWg[5];
       const double* dWj;
       if (j < 0) {
-        if (s->face_bc[f] == 1) continue;
+        if (s->face_bc[f] == 1 || s->face_bc[f] == 4) continue;   /* free-stream and outflow increments are zero */
         ghost_increment(s, f, s->dWs + 5 * i, dWg);
         dWj = dWg;
       } else {

@@ -550,38 +550,37 @@ const char* igks_kernel_name(int32_t i) {
   return (i >= 0 && i < N_KERNEL_KINDS) ? KERNEL_NAMES[i] : "";
 }
 
-int igks_mesh_upload(igks_ctx* ctx, int32_t n_nodes, const double* xy, int32_t n_cells,
-                     const int32_t* cell_ptr, const int32_t* cell_nodes, int32_t n_faces,
-                     const int32_t* face_nodes, const int32_t* face_cells, const int32_t* face_bc,
-                     int32_t* solve_id) {
-  if (!ctx) return IGKS_EINVAL;
-  if (ctx->built) return fail(ctx, IGKS_EBUSY, "mesh upload after the device data was built");
+}  // extern "C"
+
+// host-side mesh validation shared by igks_mesh_upload and the server's submit
+int igks_check_mesh_(int32_t n_nodes, const double* xy, int32_t n_cells, const int32_t* cell_ptr,
+                     const int32_t* cell_nodes, int32_t n_faces, const int32_t* face_nodes,
+                     const int32_t* face_cells, const int32_t* face_bc, std::string* msg) {
+  auto fail = [&](int code, const char* m) { *msg = m; return code; };
   if (n_nodes <= 0 || n_cells <= 0 || n_faces <= 0 || !xy || !cell_ptr || !cell_nodes || !face_nodes ||
       !face_cells || !face_bc)
-    return fail(ctx, IGKS_EINVAL, "null array or non-positive size");
-  HostMesh m;
-  m.nn = n_nodes; m.nc = n_cells; m.nf = n_faces;
-  if (cell_ptr[0] != 0) return fail(ctx, IGKS_EMESH, "cell_ptr[0] != 0");
+    return fail(IGKS_EINVAL, "null array or non-positive size");
+  if (cell_ptr[0] != 0) return fail(IGKS_EMESH, "cell_ptr[0] != 0");
   for (int i = 0; i < n_cells; i++)
-    if (cell_ptr[i + 1] - cell_ptr[i] < 3) return fail(ctx, IGKS_EMESH, "cell with fewer than 3 nodes");
+    if (cell_ptr[i + 1] - cell_ptr[i] < 3) return fail(IGKS_EMESH, "cell with fewer than 3 nodes");
   const int nk = cell_ptr[n_cells];
   for (int k = 0; k < nk; k++)
-    if (cell_nodes[k] < 0 || cell_nodes[k] >= n_nodes) return fail(ctx, IGKS_EMESH, "cell node index out of range");
+    if (cell_nodes[k] < 0 || cell_nodes[k] >= n_nodes) return fail(IGKS_EMESH, "cell node index out of range");
   std::vector<int> deg(n_cells, 0);
   for (int f = 0; f < n_faces; f++) {
     int a = face_nodes[2 * f], b = face_nodes[2 * f + 1];
     int l = face_cells[2 * f], r = face_cells[2 * f + 1];
-    if (a < 0 || a >= n_nodes || b < 0 || b >= n_nodes || a == b) return fail(ctx, IGKS_EMESH, "face node index out of range");
-    if (l < 0 || l >= n_cells) return fail(ctx, IGKS_EMESH, "face without a valid left cell");
-    if (r >= n_cells || r == l) return fail(ctx, IGKS_EMESH, "face right cell out of range");
-    if (r < 0 && (face_bc[f] < IGKS_BC_FARFIELD || face_bc[f] > IGKS_BC_WALL))
-      return fail(ctx, IGKS_EMESH, "boundary face without a boundary tag");
-    if (r >= 0 && face_bc[f] != IGKS_BC_INTERIOR) return fail(ctx, IGKS_EMESH, "interior face with a boundary tag");
+    if (a < 0 || a >= n_nodes || b < 0 || b >= n_nodes || a == b) return fail(IGKS_EMESH, "face node index out of range");
+    if (l < 0 || l >= n_cells) return fail(IGKS_EMESH, "face without a valid left cell");
+    if (r >= n_cells || r == l) return fail(IGKS_EMESH, "face right cell out of range");
+    if (r < 0 && (face_bc[f] < IGKS_BC_FARFIELD || face_bc[f] > IGKS_BC_OUTFLOW))
+      return fail(IGKS_EMESH, "boundary face without a boundary tag");
+    if (r >= 0 && face_bc[f] != IGKS_BC_INTERIOR) return fail(IGKS_EMESH, "interior face with a boundary tag");
     deg[l]++;
     if (r >= 0) deg[r]++;
   }
   for (int i = 0; i < n_cells; i++)
-    if (deg[i] != cell_ptr[i + 1] - cell_ptr[i]) return fail(ctx, IGKS_EMESH, "cell is not closed by its faces");
+    if (deg[i] != cell_ptr[i + 1] - cell_ptr[i]) return fail(IGKS_EMESH, "cell is not closed by its faces");
   // every face is an edge of its cells: a -> b in the left cell's node cycle, b -> a in the right's
   auto has_edge = [&](int c, int a, int b) {
     const int s0 = cell_ptr[c], n = cell_ptr[c + 1] - s0;
@@ -592,11 +591,34 @@ int igks_mesh_upload(igks_ctx* ctx, int32_t n_nodes, const double* xy, int32_t n
   for (int f = 0; f < n_faces; f++) {
     int a = face_nodes[2 * f], b = face_nodes[2 * f + 1];
     int l = face_cells[2 * f], r = face_cells[2 * f + 1];
-    if (!has_edge(l, a, b)) return fail(ctx, IGKS_EMESH, "face is not an edge of its left cell (a->b)");
-    if (r >= 0 && !has_edge(r, b, a)) return fail(ctx, IGKS_EMESH, "face is not an edge of its right cell (b->a)");
+    if (!has_edge(l, a, b)) return fail(IGKS_EMESH, "face is not an edge of its left cell (a->b)");
+    if (r >= 0 && !has_edge(r, b, a)) return fail(IGKS_EMESH, "face is not an edge of its right cell (b->a)");
   }
   for (int k = 0; k < 2 * n_nodes; k++)
-    if (!std::isfinite(xy[k])) return fail(ctx, IGKS_EMESH, "non-finite node coordinate");
+    if (!std::isfinite(xy[k])) return fail(IGKS_EMESH, "non-finite node coordinate");
+  return IGKS_OK;
+}
+
+bool igks_check_flow_(const igks_flow* f) {
+  return f->mach > 0 && f->reynolds > 0 && f->prandtl > 0 && f->cfl_exp > 0 && f->cfl_init > 0 &&
+         f->cfl_min > 0 && f->cfl_max >= f->cfl_min && f->limiter >= 0 && f->limiter <= 2 && f->t_ref > 0;
+}
+
+extern "C" {
+
+int igks_mesh_upload(igks_ctx* ctx, int32_t n_nodes, const double* xy, int32_t n_cells,
+                     const int32_t* cell_ptr, const int32_t* cell_nodes, int32_t n_faces,
+                     const int32_t* face_nodes, const int32_t* face_cells, const int32_t* face_bc,
+                     int32_t* solve_id) {
+  if (!ctx) return IGKS_EINVAL;
+  if (ctx->built) return fail(ctx, IGKS_EBUSY, "mesh upload after the device data was built");
+  std::string msg;
+  int vrc = igks_check_mesh_(n_nodes, xy, n_cells, cell_ptr, cell_nodes, n_faces, face_nodes, face_cells,
+                             face_bc, &msg);
+  if (vrc) return fail(ctx, vrc, msg);
+  HostMesh m;
+  m.nn = n_nodes; m.nc = n_cells; m.nf = n_faces;
+  const int nk = cell_ptr[n_cells];
   m.xy.assign(xy, xy + 2 * (size_t)n_nodes);
   m.cell_ptr.assign(cell_ptr, cell_ptr + n_cells + 1);
   m.cell_nodes.assign(cell_nodes, cell_nodes + nk);
@@ -612,9 +634,7 @@ int igks_mesh_upload(igks_ctx* ctx, int32_t n_nodes, const double* xy, int32_t n
 
 int igks_set_flow(igks_ctx* ctx, int32_t solve, const igks_flow* f) {
   if (!ctx || !f || solve < 0 || solve >= (int)ctx->meshes.size()) return IGKS_EINVAL;
-  if (!(f->mach > 0) || !(f->reynolds > 0) || !(f->prandtl > 0) || !(f->cfl_exp > 0) || !(f->cfl_init > 0) ||
-      !(f->cfl_min > 0) || f->cfl_max < f->cfl_min || f->limiter < 0 || f->limiter > 2 || !(f->t_ref > 0))
-    return fail(ctx, IGKS_EINVAL, "invalid flow conditions");
+  if (!igks_check_flow_(f)) return fail(ctx, IGKS_EINVAL, "invalid flow conditions");
   ctx->flows[solve] = *f;
   ctx->flow_set[solve] = 1;
   if (ctx->built) {
@@ -990,6 +1010,25 @@ int igks_destroy(igks_ctx* ctx) {
     if (ev) cudaEventDestroy(ev);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
+  return IGKS_OK;
+}
+
+int igks_footprint_bytes(int32_t n_nodes, int32_t n_cells, int32_t n_faces, int32_t nnz, int64_t* out) {
+  if (n_nodes <= 0 || n_cells <= 0 || n_faces <= 0 || nnz < 0 || !out) return IGKS_EINVAL;
+  const int64_t ncp = (int64_t)(n_cells + CELL_ALIGN - 1) / CELL_ALIGN * CELL_ALIGN;
+  // per padded cell: 115 doubles (state, gradients, increments, sweep records) + 32 ints
+  // (CSR pointers, orders, levels, positions, padded stencils); per CSR entry 60 B (face
+  // and node lists, sweep stencil coefficients, maps) + 40 B (one sweep entry); per face
+  // 28 doubles + 8 ints; per node 2 doubles; a few hundred bytes per solve
+  *out = 1048 * ncp + 100 * (int64_t)nnz + 256 * (int64_t)n_faces + 16 * (int64_t)n_nodes + 4096;
+  return IGKS_OK;
+}
+
+int igks_device_bytes(igks_ctx* ctx, int64_t* out) {
+  if (!ctx || !out) return IGKS_EINVAL;
+  int64_t b = 0;
+  for (const auto& x : ctx->bufs) b += (int64_t)x.bytes;
+  *out = b;
   return IGKS_OK;
 }
 

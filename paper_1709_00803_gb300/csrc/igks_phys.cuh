@@ -41,31 +41,27 @@ __device__ inline void ghost_state(const DevFlow& fl, int bc, double nx, double 
     Wg[3] = Wi[3]; Wg[4] = Wi[4];
     return;
   }
-  // characteristic far field: Riemann invariants along the outward normal
   const double g = GAMMA;
   const double* Wf = fl.Winf;
-  double ri = Wi[0], ui = Wi[1] / ri, vi = Wi[2] / ri;
-  double pi = pressure_of(Wi[0], Wi[1], Wi[2], Wi[3]);
-  double ci = sqrt(g * pi / ri);
-  double ro = Wf[0], uo = Wf[1] / ro, vo = Wf[2] / ro;
-  double po = pressure_of(Wf[0], Wf[1], Wf[2], Wf[3]);
-  double co = sqrt(g * po / ro);
-  double uni = ui * nx + vi * ny, uno = uo * nx + vo * ny;
-  if (uni <= -ci) { for (int v = 0; v < 5; v++) Wg[v] = Wf[v]; return; }
-  if (uni >= ci) { for (int v = 0; v < 5; v++) Wg[v] = Wi[v]; return; }
-  double Rp = uni + 2.0 * ci / (g - 1.0);
-  double Rm = uno - 2.0 * co / (g - 1.0);
-  double ub = 0.5 * (Rp + Rm);
-  double cb = 0.25 * (g - 1.0) * (Rp - Rm);
-  double ut, vt, ent, nut;
-  if (ub > 0.0) { ut = ui - uni * nx; vt = vi - uni * ny; ent = pi / pow(ri, g); nut = Wi[4]; }
-  else          { ut = uo - uno * nx; vt = vo - uno * ny; ent = po / pow(ro, g); nut = Wf[4]; }
-  double rb = pow(cb * cb / (g * ent), 1.0 / (g - 1.0));
-  double pb = rb * cb * cb / g;
-  double ubx = ub * nx + ut, uby = ub * ny + vt;
-  Wg[0] = rb; Wg[1] = rb * ubx; Wg[2] = rb * uby;
-  Wg[3] = pb / (g - 1.0) + 0.5 * rb * (ubx * ubx + uby * uby);
-  Wg[4] = nut;
+  if (bc == 4) {
+    // outflow (Section II.E): boundary-normal velocity from the Riemann invariants R+
+    // (inside) and R- (free stream); density, tangential velocity, internal energy per
+    // unit volume (the temperature, lambda) and nu_tilde from inside
+    double ri = Wi[0], ui = Wi[1] / ri, vi = Wi[2] / ri;
+    double ei = Wi[3] - 0.5 * ri * (ui * ui + vi * vi);
+    double ci = sqrt(g * (g - 1.0) * ei / ri);
+    double po = pressure_of(Wf[0], Wf[1], Wf[2], Wf[3]);
+    double co = sqrt(g * po / Wf[0]);
+    double uni = ui * nx + vi * ny, uno = (Wf[1] * nx + Wf[2] * ny) / Wf[0];
+    double ub = 0.5 * ((uni + 2.0 * ci / (g - 1.0)) + (uno - 2.0 * co / (g - 1.0)));
+    double bx = ub * nx + (ui - uni * nx), by = ub * ny + (vi - uni * ny);
+    Wg[0] = ri; Wg[1] = ri * bx; Wg[2] = ri * by;
+    Wg[3] = ei + 0.5 * ri * (bx * bx + by * by);
+    Wg[4] = Wi[4];
+    return;
+  }
+  // free stream (Section II.E)
+  for (int v = 0; v < 5; v++) Wg[v] = Wf[v];
 }
 
 }  // namespace igks

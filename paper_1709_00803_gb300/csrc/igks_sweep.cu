@@ -196,7 +196,7 @@ __device__ __forceinline__ void bwd_cell(const Dev& d, int i, bool sa_on) {
       if (j <= i) continue;
     } else {
       const int f = d.cf_face[k];
-      if (d.fbc[f] == 1) continue;                   // far-field increments are zero
+      if (d.fbc[f] == 1 || d.fbc[f] == 4) continue;  // free-stream and outflow increments are zero
       j = -1 - f;
     }
     bwd_entry<T>(d, nullptr, dF, dWo, j, -1, ws, sc[k], sc[nnz + k], sc[2 * nnz + k], sc[3 * nnz + k], sa_on, acc);

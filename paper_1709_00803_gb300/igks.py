@@ -12,7 +12,7 @@ import numpy as np
 from . import build as _build
 
 OK, CONVERGED = 0, 1
-EINVAL, EMESH, ENOMEM, ECUDA, DIVERGED, TIMEOUT, EBUSY = -1, -2, -3, -4, -5, -6, -7
+EINVAL, EMESH, ENOMEM, ECUDA, DIVERGED, TIMEOUT, EBUSY, MAXITER = -1, -2, -3, -4, -5, -6, -7, -8
 PREC_FP64, PREC_MIXED = 0, 1
 ARR = dict(grad=1, phi=2, lambda_f=3, lambda_c=4, flux=5, res=6, dwstar=7, dw=8, ghost=9,
            geom_cell=10, geom_face=11)
@@ -48,6 +48,40 @@ class Status(C.Structure):
     _fields_ = [("iters", C.c_int32), ("state", C.c_int32), ("res_l2_rho", C.c_double),
                 ("res_l2_rel", C.c_double), ("res_inf", C.c_double), ("eq40_ratio", C.c_double),
                 ("cfl", C.c_double), ("dt", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerOptions(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("max_slots", C.c_int32),
+                ("max_cohort", C.c_int32), ("iters_per_step", C.c_int32), ("max_iters", C.c_int32),
+                ("hbm_budget", C.c_int64), ("repack_fraction", C.c_double), ("keep_fields", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
+
+
+class Request(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("xy", C.c_void_p), ("n_cells", C.c_int32), ("cell_ptr", C.c_void_p),
+                ("cell_nodes", C.c_void_p), ("n_faces", C.c_int32), ("face_nodes", C.c_void_p),
+                ("face_cells", C.c_void_p), ("face_bc", C.c_void_p), ("flow", Flow), ("tag", C.c_int64)]
+
+
+class Result(C.Structure):
+    _fields_ = [("id", C.c_int64), ("tag", C.c_int64), ("state", C.c_int32), ("iters", C.c_int32),
+                ("n_cells", C.c_int32), ("cohort", C.c_int32), ("res_l2_rel", C.c_double),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_finish", C.c_double),
+                ("forces", C.c_double * 3), ("footprint", C.c_int64)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "forces"}
+        d["forces"] = tuple(self.forces)
+        return d
+
+
+class ServerStatus(C.Structure):
+    _fields_ = [("queued", C.c_int32), ("live", C.c_int32), ("cohorts", C.c_int32), ("finished", C.c_int32),
+                ("bytes", C.c_int64), ("budget", C.c_int64), ("admitted", C.c_int32), ("repacked", C.c_int32),
+                ("step_s", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -90,6 +124,23 @@ def lib():
         L.igks_autotune.restype = C.c_int32
         L.igks_order_cells.argtypes = [i32, i32, ip, i32, ip, ip]
         L.igks_order_cells.restype = C.c_int32
+        i64p = P(C.c_int64)
+        L.igks_footprint_bytes.argtypes = [i32, i32, i32, i32, i64p]
+        L.igks_device_bytes.argtypes = [vp, i64p]
+        L.igks_server_create.argtypes = [P(ServerOptions), P(vp)]
+        L.igks_server_submit.argtypes = [vp, P(Request), i64p]
+        L.igks_server_step.argtypes = [vp, P(ServerStatus)]
+        L.igks_server_poll.argtypes = [vp, P(Result), i32, ip]
+        L.igks_server_take_fields.argtypes = [vp, C.c_int64, dp]
+        L.igks_server_now.argtypes = [vp, dp]
+        L.igks_server_get_status.argtypes = [vp, P(ServerStatus)]
+        L.igks_server_destroy.argtypes = [vp]
+        L.igks_server_last_error.argtypes = [vp]
+        L.igks_server_last_error.restype = C.c_char_p
+        for name in ("igks_footprint_bytes", "igks_device_bytes", "igks_server_create", "igks_server_submit",
+                     "igks_server_step", "igks_server_poll", "igks_server_take_fields", "igks_server_now",
+                     "igks_server_get_status", "igks_server_destroy"):
+            getattr(L, name).restype = C.c_int32
         for name in ("igks_create", "igks_mesh_upload", "igks_set_flow", "igks_init_freestream",
                      "igks_iterate", "igks_get_fields", "igks_set_fields", "igks_get_scalars",
                      "igks_set_scalars", "igks_get_array", "igks_mesh_info", "igks_get_forces",
@@ -251,6 +302,11 @@ class Context:
         self._check(lib().igks_get_forces(self.h, solve, bc_tag, _dp(o)))
         return dict(cl=o[0], cd=o[1], cd_viscous=o[2])
 
+    def device_bytes(self):
+        o = C.c_int64()
+        self._check(lib().igks_device_bytes(self.h, C.byref(o)))
+        return o.value
+
     def launches_per_iteration(self):
         o = C.c_int32()
         self._check(lib().igks_launches_per_iteration(self.h, C.byref(o)))
@@ -259,6 +315,88 @@ class Context:
     def destroy(self):
         if getattr(self, "h", None):
             lib().igks_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def footprint_bytes(mesh) -> int:
+    """igks_footprint_bytes: upper bound of the device bytes of one solve of this mesh."""
+    o = C.c_int64()
+    rc = lib().igks_footprint_bytes(mesh.n_nodes, mesh.n_cells, mesh.n_faces, int(mesh.cell_ptr[-1]), C.byref(o))
+    if rc != OK:
+        raise IgksError(rc, "igks_footprint_bytes failed")
+    return o.value
+
+
+class Server:
+    """One igks_server: continuous batching of steady solves on one GPU."""
+
+    def __init__(self, precision=PREC_MIXED, device=0, max_slots=64, max_cohort=64, iters_per_step=20,
+                 max_iters=50000, hbm_budget=0, repack_fraction=0.5, keep_fields=1):
+        o = ServerOptions(precision=precision, device=device, max_slots=max_slots, max_cohort=max_cohort,
+                          iters_per_step=iters_per_step, max_iters=max_iters, hbm_budget=hbm_budget,
+                          repack_fraction=repack_fraction, keep_fields=keep_fields)
+        h = C.c_void_p()
+        rc = lib().igks_server_create(C.byref(o), C.byref(h))
+        if rc:
+            raise IgksError(rc, "igks_server_create failed")
+        self.h = h
+        self._keep = {}
+
+    def _check(self, rc):
+        if rc != OK:
+            raise IgksError(rc, lib().igks_server_last_error(self.h).decode())
+        return rc
+
+    def submit(self, mesh, flow, tag=0) -> int:
+        arrs = (np.ascontiguousarray(mesh.xy, dtype=np.float64).ravel(),
+                np.ascontiguousarray(mesh.cell_ptr, dtype=np.int32),
+                np.ascontiguousarray(mesh.cell_nodes, dtype=np.int32),
+                np.ascontiguousarray(mesh.face_nodes, dtype=np.int32).ravel(),
+                np.ascontiguousarray(mesh.face_cells, dtype=np.int32).ravel(),
+                np.ascontiguousarray(mesh.face_bc, dtype=np.int32))
+        xy, cp, cn, fn, fc, fb = (a.ctypes.data for a in arrs)
+        r = Request(n_nodes=mesh.n_nodes, xy=xy, n_cells=mesh.n_cells, cell_ptr=cp, cell_nodes=cn,
+                    n_faces=mesh.n_faces, face_nodes=fn, face_cells=fc, face_bc=fb, flow=to_flow(flow), tag=tag)
+        rid = C.c_int64()
+        self._check(lib().igks_server_submit(self.h, C.byref(r), C.byref(rid)))
+        self._keep[rid.value] = mesh.n_cells
+        return rid.value
+
+    def step(self):
+        st = ServerStatus()
+        self._check(lib().igks_server_step(self.h, C.byref(st)))
+        return st.as_dict()
+
+    def status(self):
+        st = ServerStatus()
+        self._check(lib().igks_server_get_status(self.h, C.byref(st)))
+        return st.as_dict()
+
+    def poll(self, cap=256):
+        out = (Result * cap)()
+        n = C.c_int32()
+        self._check(lib().igks_server_poll(self.h, out, cap, C.byref(n)))
+        return [out[k].as_dict() for k in range(n.value)]
+
+    def take_fields(self, rid):
+        W = np.zeros((5, self._keep[rid]))
+        self._check(lib().igks_server_take_fields(self.h, rid, _dp(W)))
+        return W
+
+    def now(self):
+        t = C.c_double()
+        self._check(lib().igks_server_now(self.h, C.byref(t)))
+        return t.value
+
+    def destroy(self):
+        if getattr(self, "h", None):
+            lib().igks_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -26,7 +26,10 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header(tmp_path):
     """sizeof and field offsets as the C compiler lays them out, against ctypes."""
     from paper_1709_00803_gb300 import igks
-    checks = {"igks_flow": igks.Flow, "igks_status": igks.Status, "igks_options": igks.Options}
+    checks = {"igks_flow": igks.Flow, "igks_status": igks.Status, "igks_options": igks.Options,
+              "igks_tuning": igks.Tuning, "igks_server_options": igks.ServerOptions,
+              "igks_request": igks.Request, "igks_result": igks.Result,
+              "igks_server_status": igks.ServerStatus}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "igks.h"', "int main(void){"]
     for cname, py in checks.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -57,3 +60,14 @@ def test_oracle_and_library_share_no_code():
     for f in ("igks_oracle.c", "igks_oracle.h", "__init__.py"):
         txt = open(os.path.join(ROOT, "oracle", f)).read()
         assert "paper_1709_00803_gb300" not in txt and "igks_dev" not in txt and "igks.h" not in txt, f
+
+
+def test_footprint_bound_is_host_only_and_monotone():
+    """igks_footprint_bytes runs on the host (no GPU needed) and grows with every size."""
+    from paper_1709_00803_gb300 import igks
+    from igks_inputs import meshgen as G
+    small, big = G.laminar_plate(), G.turbulent_plate()
+    a, b = igks.footprint_bytes(small), igks.footprint_bytes(big)
+    assert 0 < a < b
+    # about 2 kB per cell for these meshes: one 250k-cell solve takes well under 1 GB
+    assert 1500 < b / big.n_cells < 2500

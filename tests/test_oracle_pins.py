@@ -234,3 +234,106 @@ def test_flux_ns_limit_heat_flux_with_prandtl_fix(ratio):
     assert abs(Fx[3] - ref) <= 5.0 / ratio * abs(ref) + 1e-9 * abs(ref)
     # the unfixed (BGK, Pr = 1) heat flux is Pr times smaller
     assert abs(heat - ref * fl.prandtl) <= 5.0 / ratio * abs(ref)
+
+
+# --- boundary conditions (Section II.E) -------------------------------------------------
+
+def _ghosts_of_uniform(W0, bcs=("wall", "outflow"), flow=None):
+    """Ghost states the oracle builds from a uniform interior state W0 on a 2 x 2 quad mesh
+    whose bottom is `bcs[0]` and whose other sides are `bcs[1]`."""
+    from igks_inputs import meshgen as G
+    m = G.tiny_quads(2, 2, bcs=bcs)
+    fl = flow or F.laminar_plate_flow()
+    o = O.Oracle(m, fl)
+    o.set_W(np.repeat(np.asarray(W0, dtype=np.float64)[:, None], m.n_cells, axis=1))
+    o.iterate(1)
+    return m, fl, o.get(O.ORA_GHOST)
+
+
+def _conserved(r, u, v, p, nut=0.0):
+    return [r, r * u, r * v, p / (F.GAMMA - 1.0) + 0.5 * r * (u * u + v * v), nut]
+
+
+def _prim(W):
+    r, u, v = W[0], W[1] / W[0], W[2] / W[0]
+    return r, u, v, (F.GAMMA - 1.0) * (W[3] - 0.5 * r * (u * u + v * v))
+
+
+def _outflow_faces(m):
+    from igks_inputs import meshgen as G
+    return np.nonzero((m.face_cells[:, 1] < 0) & (m.face_bc == G.BC_OUTFLOW))[0]
+
+
+def _face_normal(m, f):
+    a, b = m.face_nodes[f]
+    d = m.xy[b] - m.xy[a]
+    n = np.array([d[1], -d[0]])          # right of a -> b: out of the left cell
+    return n / np.linalg.norm(n)
+
+
+def test_free_stream_ghosts_hold_the_free_stream():
+    """Free-stream boundary: the ghost is the free stream whatever the interior holds."""
+    fl = F.laminar_plate_flow()
+    r, u, v, p = 1.2, 0.6, -0.3, 1.3 / (F.GAMMA * fl.mach ** 2)
+    m, fl, gh = _ghosts_of_uniform(_conserved(r, u, v, p), bcs=("wall", "farfield"), flow=fl)
+    Winf = F.uniform_state(m, fl)[:, 0]
+    far = np.nonzero(m.face_bc == 1)[0]
+    assert len(far) > 0
+    np.testing.assert_allclose(gh[:, far], np.repeat(Winf[:, None], len(far), axis=1), rtol=0, atol=1e-14 * Winf[3])
+
+
+def test_outflow_ghost_of_the_free_stream_is_the_free_stream():
+    fl = F.laminar_plate_flow()
+    from igks_inputs import meshgen as G
+    m0 = G.tiny_quads(2, 2, bcs=("wall", "outflow"))
+    Winf = F.uniform_state(m0, fl)[:, 0]
+    m, fl, gh = _ghosts_of_uniform(Winf, flow=fl)
+    out = _outflow_faces(m)
+    assert len(out) >= 4
+    for f in out:
+        np.testing.assert_allclose(gh[:, f], Winf, rtol=1e-14, atol=1e-14)
+
+
+def test_outflow_ghost_passes_inside_values_and_averages_the_invariants():
+    """Outflow boundary: density, pressure (through lambda) and tangential velocity come
+    from inside; the normal velocity is the mean of the two Riemann invariants, so it
+    moves by half of a change of the inside normal velocity and by 1/(gamma-1) of a change
+    of the inside sound speed, and does not depend on the inside tangential velocity."""
+    fl = F.laminar_plate_flow()
+    g = F.GAMMA
+    p_inf = 1.0 / (g * fl.mach ** 2)
+    base = dict(r=1.1, u=0.8, v=0.15, p=1.04 * p_inf)
+
+    def ghosts(**kw):
+        q = dict(base, **kw)
+        m, _, gh = _ghosts_of_uniform(_conserved(q["r"], q["u"], q["v"], q["p"]), flow=fl)
+        return m, gh
+
+    m, gh0 = ghosts()
+    out = _outflow_faces(m)
+    for f in out:
+        n = _face_normal(m, f)
+        t = np.array([-n[1], n[0]])
+        r, u, v, p = _prim(gh0[:, f])
+        assert abs(r - base["r"]) <= 1e-14
+        assert abs(p - base["p"]) <= 1e-12 * base["p"]
+        assert abs((u * t[0] + v * t[1]) - (base["u"] * t[0] + base["v"] * t[1])) <= 1e-13
+    # responses of the normal velocity, by finite differences of the inside state
+    eps = 1e-6
+    for f in out:
+        n = _face_normal(m, f)
+        t = np.array([-n[1], n[0]])
+        un0 = (gh0[1, f] * n[0] + gh0[2, f] * n[1]) / gh0[0, f]
+        # inside normal velocity + eps
+        m1, gh1 = ghosts(u=base["u"] + eps * n[0], v=base["v"] + eps * n[1])
+        un1 = (gh1[1, f] * n[0] + gh1[2, f] * n[1]) / gh1[0, f]
+        assert abs((un1 - un0) / eps - 0.5) < 1e-6
+        # inside tangential velocity + eps: no change of the normal velocity
+        m2, gh2 = ghosts(u=base["u"] + eps * t[0], v=base["v"] + eps * t[1])
+        un2 = (gh2[1, f] * n[0] + gh2[2, f] * n[1]) / gh2[0, f]
+        assert abs(un2 - un0) < 1e-12
+        # inside sound speed c -> c (1 + eps) at fixed density: pressure scales by (1+eps)^2
+        c0 = math.sqrt(g * base["p"] / base["r"])
+        m3, gh3 = ghosts(p=base["p"] * (1 + eps) ** 2)
+        un3 = (gh3[1, f] * n[0] + gh3[2, f] * n[1]) / gh3[0, f]
+        assert abs((un3 - un0) / (c0 * eps) - 1.0 / (g - 1.0)) < 1e-5
