@@ -332,7 +332,15 @@ def main():
     ap.add_argument("--impl", default="igks", choices=["igks", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="headline sweep precision (the other one is measured too)")
-    ap.add_argument("--workload", default="turbulent_plate", choices=list(WORKLOADS) + ["naca_batch"])
+    ap.add_argument("--workload", default="turbulent_plate", choices=list(WORKLOADS) + ["naca_batch", "serving"])
+    ap.add_argument("--requests", type=int, default=16, help="requests of the serving workload")
+    ap.add_argument("--cells-lo", type=int, default=2000)
+    ap.add_argument("--cells-hi", type=int, default=30000)
+    ap.add_argument("--slots", type=int, default=64, help="serving: live solves at most")
+    ap.add_argument("--iters-per-step", type=int, default=100)
+    ap.add_argument("--max-iters", type=int, default=20000)
+    ap.add_argument("--eq40", type=float, default=3e-8,
+                    help="serving: also stop at the paper's Eq. 40 ratio (0: residual 1e-10 only)")
     ap.add_argument("--batch", type=int, default=64, help="solves of the naca_batch workload")
     ap.add_argument("--ordering", default="as_given", choices=["as_given", "multicolor"],
                     help="cell numbering = LU-SGS sweep order (the oracle baseline runs the same)")
@@ -343,6 +351,8 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.workload == "naca_batch":
         return main_batch(args)
+    if args.workload == "serving":
+        return main_serving(args)
     mk, fl_fn, desc = WORKLOADS[args.workload]
     mesh, flow = mk(), fl_fn()
     if args.ordering == "multicolor":
@@ -431,6 +441,140 @@ def main_batch(args):
         dist.barrier()
         dist.destroy_process_group()
 
+
+def serving_cases(n, cells_lo, cells_hi, eq40_target):
+    """The serving request stream: seeded flat plates and NACA sections (SA), flow and size
+    drawn per request; each flow stops at res_target (1e-10) or, when eq40_target > 0, at
+    the paper's Eq. 40 criterion, whichever comes first."""
+    cases = []
+    for sp in G.serving_specs(n, 5, cells_lo, cells_hi):
+        if sp["kind"] == "plate":
+            mesh = G.plate_scaled(sp["cells"], sp["mesh_seed"])
+            fl = F.turbulent_plate_flow()
+            fl.mach, fl.reynolds = sp["mach"], sp["reynolds"]
+        else:
+            mesh = G.naca_scaled(sp["m"], sp["p"], sp["t"], sp["cells"], sp["mesh_seed"])
+            fl = F.naca_flow(mach=sp["mach"], reynolds=sp["reynolds"], aoa_deg=sp["aoa"])
+        fl.eq40_target = eq40_target
+        cases.append((mesh, fl, sp))
+    return cases
+
+
+def _pct(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
+
+
+def _serve(igks, cases, args, arrivals=None):
+    """Run the request stream through one server (mixed precision). arrivals=None submits
+    everything at once (capacity); otherwise request k is submitted once the server clock
+    passes arrivals[k]. Returns the results and the makespan."""
+    srv = igks.Server(precision=igks.PREC_MIXED, max_slots=args.slots, max_cohort=args.slots,
+                      iters_per_step=args.iters_per_step, max_iters=args.max_iters, keep_fields=0)
+    n = len(cases)
+    start = srv.now()
+    nxt, results = 0, []
+    if arrivals is None:
+        for k, (m, fl, _) in enumerate(cases):
+            srv.submit(m, fl, tag=k)
+        nxt = n
+    while len(results) < n:
+        now = srv.now() - start
+        while nxt < n and arrivals[nxt] <= now:
+            srv.submit(cases[nxt][0], cases[nxt][1], tag=nxt)
+            nxt += 1
+        st = srv.status()
+        if st["live"] + st["queued"] == 0:
+            time.sleep(max(0.0, min(0.05, arrivals[nxt] - now)))
+            continue
+        srv.step()
+        results += srv.poll()
+    srv.destroy()
+    for r in results:
+        r["t_arrival"] = (arrivals[r["tag"]] if arrivals is not None else 0.0) + start
+    return results, max(r["t_finish"] for r in results) - start
+
+
+def _plain(igks, cases, args):
+    """The plain path: each request alone, FP64 sweeps, one after the other."""
+    out = []
+    for m, fl, _ in cases:
+        t = time.perf_counter()
+        ctx = igks.Context(precision=igks.PREC_FP64, check_every=100)
+        sid = ctx.mesh_upload(m); ctx.set_flow(sid, fl); ctx.init_freestream(sid)
+        rc, st = ctx.iterate(args.max_iters)
+        ctx.destroy()
+        out.append(dict(service=time.perf_counter() - t, state=st[sid]["state"], iters=st[sid]["iters"]))
+    return out
+
+
+def main_serving(args):
+    """Continuous batching of a Poisson stream of steady solves against the plain
+    one-solve-at-a-time FP64 path on the same GPU."""
+    import torch
+    from paper_1709_00803_gb300 import igks
+    dist, rank, ws = _dist()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    all_cases = serving_cases(args.requests, args.cells_lo, args.cells_hi, args.eq40)
+    cases = all_cases[rank::ws]          # replicas: each rank serves its share of the stream
+    conv = lambda st: st == igks.CONVERGED
+    # capacity: everything submitted at once
+    with ClockSampler(dev) as clk:
+        res_cap, T_cap = _serve(igks, cases, args)
+    n_conv = sum(conv(r["state"]) for r in res_cap)
+    cap_per_s = len(res_cap) / T_cap
+    # open loop: Poisson arrivals at 0.8 x the measured capacity
+    gaps = np.array([sp["gap"] for _, _, sp in cases])
+    arrivals = np.cumsum(gaps) / (0.8 * cap_per_s)
+    res_open, T_open = _serve(igks, cases, args, arrivals)
+    lat = [r["t_finish"] - r["t_arrival"] for r in res_open if conv(r["state"])]
+    # plain FP64, one at a time; its latency under the same arrivals follows from its
+    # service times (one FIFO server)
+    plain = _plain(igks, cases, args)
+    fin, lat_plain = 0.0, []
+    for a, p in zip(arrivals, plain):
+        fin = max(fin, a) + p["service"]
+        if conv(p["state"]):
+            lat_plain.append(fin - a)
+    T_plain = sum(p["service"] for p in plain)
+    n_plain = sum(conv(p["state"]) for p in plain)
+    loc = dict(n=len(cases), conv=n_conv, T_cap=T_cap, lat=lat, conv_plain=n_plain, T_plain=T_plain,
+               lat_plain=lat_plain, cells=sum(m.n_cells for m, _, _ in cases),
+               iters=[r["iters"] for r in res_cap], states=[r["state"] for r in res_cap],
+               clocks=clk.summary())
+    parts = [loc]
+    if dist:
+        parts = [None] * ws
+        dist.all_gather_object(parts, loc)
+    T = max(p["T_cap"] for p in parts)
+    served = sum(p["conv"] for p in parts) / T * 3600.0
+    plain_rate = sum(p["conv_plain"] for p in parts) / max(p["T_plain"] for p in parts) * 3600.0
+    lat_all = sum((p["lat"] for p in parts), [])
+    latp_all = sum((p["lat_plain"] for p in parts), [])
+    stop = "density residual 1e-10" + (f" or Eq. 40 ratio <= {args.eq40:g}" if args.eq40 > 0 else "")
+    out = {"metric": "converged solves/hour", "value": served, "unit": "solves/hour", "n_gpus": ws,
+           "steps": None, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64 flux/residual/update + f32 sweeps", "data": "synthetic",
+           "config": {"workload": f"{args.requests} seeded requests (flat plate or NACA 4-digit, SA; cells "
+                                  f"log-uniform {args.cells_lo}-{args.cells_hi}; Ma 0.1-0.75, AoA -4..8, "
+                                  f"Re 1e6-1e7), stop at {stop}, cap {args.max_iters} iterations",
+                      "slots": args.slots, "iters_per_step": args.iters_per_step},
+           "served": {"solves_per_hour": served, "converged": sum(p["conv"] for p in parts),
+                      "requests": sum(p["n"] for p in parts), "makespan_s": T,
+                      "p50_s": _pct(lat_all, 50), "p99_s": _pct(lat_all, 99),
+                      "arrival_rate_per_s": 0.8 * sum(p["n"] for p in parts) / T},
+           "plain_fp64_one_at_a_time": {"solves_per_hour": plain_rate,
+                                        "converged": sum(p["conv_plain"] for p in parts),
+                                        "busy_s": max(p["T_plain"] for p in parts),
+                                        "p50_s": _pct(latp_all, 50), "p99_s": _pct(latp_all, 99)},
+           "served_over_plain": served / plain_rate if plain_rate > 0 else None,
+           "iterations": sum((p["iters"] for p in parts), []), "states": sum((p["states"] for p in parts), []),
+           "clocks": parts[0]["clocks"]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
 
 if __name__ == "__main__":
     main()

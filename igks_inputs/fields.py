@@ -36,6 +36,7 @@ class Flow:
     venkat_k: float = 5.0
     c_num: float = 1.0             # numerical collision-time coefficient
     visc_sr: int = 0               # add the viscous spectral radius to lambda_f
+    eq40_target: float = 0.0       # if > 0, also stop at the Eq. 40 ratio <= this (paper: 3e-8)
 
     def as_dict(self) -> dict:
         return asdict(self)
@@ -52,9 +53,11 @@ def turbulent_plate_flow() -> Flow:
 
 
 def naca_flow(mach: float = 0.15, reynolds: float = 6e6, aoa_deg: float = 10.0) -> Flow:
+    # the airfoils use the limiter of Eq. 9 (Barth-Jespersen reading): unlimited, the wall
+    # cells at the leading- and trailing-edge stagnation regions of these O-meshes fall
+    # into an oscillation below Ma ~0.2 that stops the residual from converging
     return Flow(mach=mach, reynolds=reynolds, aoa_deg=aoa_deg, sa_on=1, nut_ratio_inf=3.0,
-                cfl_init=10.0, cfl_min=10.0, cfl_max=1000.0, visc_sr=1,
-                limiter=LIMITER_VENKAT if mach > 0.5 else LIMITER_NONE)
+                cfl_init=10.0, cfl_min=10.0, cfl_max=1000.0, visc_sr=1, limiter=LIMITER_BJ)
 
 
 def _node_average_centres(mesh) -> np.ndarray:

@@ -546,6 +546,20 @@ def naca_scaled(m: float, p: float, t: float, target_cells: int, seed: int, name
                       name=name or f"naca{m:.3f}_{p:.2f}_{t:.2f}_{n_around}x{n_quad}+{n_rings}")
 
 
+def plate_scaled(target_cells: int, seed: int, name: str = "") -> Mesh:
+    """A hybrid flat plate built like the 20480-cell turbulent plate with its point and
+    layer counts scaled by sqrt(target_cells / 20480) (cells = nx (nq + 2 ntri_rows)),
+    keeping the quad layer as thick as the full-size one (first spacing 1e-6)."""
+    s = math.sqrt(target_cells / 20480.0)
+    nx = max(16, int(round(128 * s)))
+    nq = max(8, int(round(64 * s)))
+    ntri = max(4, int(round(48 * s)))
+    height = geometric_levels(1e-6, 1.15, 64)[-1]
+    ratio = _solve_ratio(1e-6, height, nq)
+    return flat_plate_hybrid(nx=nx, nq=nq, ntri_rows=ntri, first=1e-6, ratio=ratio, seed=seed,
+                             name=name or f"plate_{nx}x{nq}+{ntri}")
+
+
 def naca_batch_specs(n: int = 64, seed: int = 4, cells_lo: int = 8000, cells_hi: int = 80000):
     """Seeded parameters of the batched-airfoil workload: per case the NACA 4-digit shape
     (m in [0, 0.06], p in [0.2, 0.6], t in [0.08, 0.18]), the flow (Ma in [0.1, 0.75],
@@ -561,3 +575,23 @@ def naca_batch_specs(n: int = 64, seed: int = 4, cells_lo: int = 8000, cells_hi:
             cells=int(round(10 ** rng.uniform(math.log10(cells_lo), math.log10(cells_hi)))),
             mesh_seed=1000 * seed + i))
     return specs
+
+
+def serving_specs(n: int = 200, seed: int = 5, cells_lo: int = 2000, cells_hi: int = 250000):
+    """Seeded request stream of the serving workload: per request a case (flat plate or
+    NACA 4-digit section, probability 1/2 each), a target cell count log-uniform in
+    [cells_lo, cells_hi], the flow (Ma in [0.1, 0.75], AoA in [-4, 8] deg for sections and
+    0 for plates, Re log-uniform in [1e6, 1e7]), the section shape (m in [0, 0.06], p in
+    [0.2, 0.6], t in [0.08, 0.18]) and an exponential inter-arrival gap of mean 1 (the
+    caller scales it to the arrival rate). Request i uses seed 1000 * seed + i for its mesh."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        out.append(dict(
+            kind="plate" if rng.uniform() < 0.5 else "naca",
+            cells=int(round(10 ** rng.uniform(math.log10(cells_lo), math.log10(cells_hi)))),
+            mach=float(rng.uniform(0.1, 0.75)), aoa=float(rng.uniform(-4.0, 8.0)),
+            reynolds=float(10 ** rng.uniform(6.0, 7.0)),
+            m=float(rng.uniform(0.0, 0.06)), p=float(rng.uniform(0.2, 0.6)), t=float(rng.uniform(0.08, 0.18)),
+            gap=float(rng.exponential(1.0)), mesh_seed=1000 * seed + i))
+    return out

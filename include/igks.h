@@ -88,6 +88,7 @@ typedef struct igks_flow {
   double c_num;            /* numerical collision time coefficient (pressure-jump term) */
   int32_t visc_sr;         /* add the viscous term to the face spectral radius */
   int32_t pad_;
+  double eq40_target;      /* if > 0, also stop when the Eq. 40 ratio of an update is <= it */
 } igks_flow;
 
 typedef struct igks_status {

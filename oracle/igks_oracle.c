@@ -1099,7 +1099,8 @@ int ora_iterate(ora_solver* s, int n_iter) {
     step_update(s);
     s->iter++;
     if (s->status < 0) return s->status;
-    if (s->res_l2_first > 0.0 && s->res_l2 <= s->flow.res_target * s->res_l2_first) {
+    if ((s->res_l2_first > 0.0 && s->res_l2 <= s->flow.res_target * s->res_l2_first) ||
+        (s->flow.eq40_target > 0.0 && s->eq40 <= s->flow.eq40_target)) {
       s->status = 1;
       return 1;
     }

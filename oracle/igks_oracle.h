@@ -21,6 +21,7 @@ typedef struct ora_flow {
   double venkat_k, c_num;
   int visc_sr;
   int pad_;
+  double eq40_target;   /* if > 0: also converged when the Eq. 40 ratio is <= it */
 } ora_flow;
 
 typedef struct ora_solver ora_solver;

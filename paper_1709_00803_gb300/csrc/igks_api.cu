@@ -94,7 +94,7 @@ static igks_flow default_flow() {
   f.mach = 0.15; f.reynolds = 1e5; f.aoa_deg = 0.0; f.prandtl = 0.72;
   f.t_ref = 288.15; f.s_suth = 110.4; f.sa_on = 0; f.limiter = 0; f.nut_ratio_inf = 3.0;
   f.cfl_exp = 1.0; f.cfl_init = 100.0; f.cfl_min = 100.0; f.cfl_max = 100.0;
-  f.res_target = 1e-10; f.venkat_k = 5.0; f.c_num = 1.0; f.visc_sr = 0;
+  f.res_target = 1e-10; f.venkat_k = 5.0; f.c_num = 1.0; f.visc_sr = 0; f.eq40_target = 0.0;
   return f;
 }
 
@@ -114,6 +114,7 @@ static DevFlow make_devflow(const igks_flow& f) {
   d.Winf[4] = d.nut_inf;
   d.cfl_exp = f.cfl_exp; d.cfl_init = f.cfl_init; d.cfl_min = f.cfl_min; d.cfl_max = f.cfl_max;
   d.res_target = f.res_target; d.venkat_k = f.venkat_k; d.c_num = f.c_num;
+  d.eq40_target = f.eq40_target;
   d.sa_on = f.sa_on; d.limiter = f.limiter; d.visc_sr = f.visc_sr;
   return d;
 }
@@ -601,7 +602,8 @@ int igks_check_mesh_(int32_t n_nodes, const double* xy, int32_t n_cells, const i
 
 bool igks_check_flow_(const igks_flow* f) {
   return f->mach > 0 && f->reynolds > 0 && f->prandtl > 0 && f->cfl_exp > 0 && f->cfl_init > 0 &&
-         f->cfl_min > 0 && f->cfl_max >= f->cfl_min && f->limiter >= 0 && f->limiter <= 2 && f->t_ref > 0;
+         f->cfl_min > 0 && f->cfl_max >= f->cfl_min && f->limiter >= 0 && f->limiter <= 2 && f->t_ref > 0 &&
+         f->eq40_target >= 0;
 }
 
 extern "C" {

@@ -400,6 +400,8 @@ __global__ void k_end_iter(Dev d) {
   SolveState& st = d.st[s];
   if (st.state != 0) return;
   st.eq40 = __longlong_as_double((long long)d.eq40_bits[s]);
+  const double e40 = d.flow[s].eq40_target;
+  if (st.pending == 0 && e40 > 0.0 && st.eq40 <= e40) st.pending = 1;   // Eq. 40 criterion
   if (d.bad[s]) st.pending = -5;   // IGKS_DIVERGED
   st.iter += 1;
   st.state = st.pending;

@@ -25,7 +25,7 @@ constexpr double SA_CW2 = 0.3, SA_CW3 = 2.0, SA_CV1 = 7.1, SA_CV2 = 0.7, SA_CV3 
 struct DevFlow {
   double mach, re, prandtl, s_star, lam_inf, mu_inf, nut_inf, p_inf;
   double Winf[5];
-  double cfl_exp, cfl_init, cfl_min, cfl_max, res_target, venkat_k, c_num;
+  double cfl_exp, cfl_init, cfl_min, cfl_max, res_target, venkat_k, c_num, eq40_target;
   int sa_on, limiter, visc_sr, pad;
 };
 

@@ -56,3 +56,24 @@ def test_converged_fields_match_oracle(oracle_solutions, name, precision, tol):
     if precision == 0:
         # same iterates as the oracle: the stopping iteration agrees up to a threshold tie
         assert abs(st[sid]["iters"] - it_ref) <= 1
+
+
+def test_eq40_stopping_rule_matches_oracle():
+    """The paper's own criterion (Eq. 40: largest relative change of an update) as an
+    alternative stopping rule: both sides stop at the same iteration with the same fields."""
+    from paper_1709_00803_gb300 import igks
+    fl = _flow(CASES["plate24x12_Ma0.3_Re2e3"])
+    fl.eq40_target = 1e-6
+    fl.res_target = 1e-300            # only Eq. 40 can stop it
+    m = G.flat_plate_quads(24, 12, 1.15)
+    o = O.Oracle(m, fl)
+    assert o.iterate(6000) == 1
+    it_ref = int(o.scalars()["iter"])
+    ctx = igks.Context(precision=0, check_every=25)
+    sid = ctx.mesh_upload(m); ctx.set_flow(sid, fl); ctx.init_freestream(sid)
+    rc, st = ctx.iterate(6000)
+    assert rc == igks.CONVERGED and st[sid]["eq40_ratio"] <= 1e-6
+    assert abs(st[sid]["iters"] - it_ref) <= 1
+    if st[sid]["iters"] == it_ref:
+        err = _rel_l2(ctx.get_fields(sid)[:4], o.get(O.ORA_W)[:4])
+        assert np.all(err <= 1e-10), err
