@@ -66,11 +66,22 @@ def alg_bytes(kernel, t, nc, nf):
     return per.get(kernel)
 
 
-def _dist():
+def _max_over_ranks(dist, x, device):
+    """The largest x over all ranks (x itself without a process group): every timed
+    quantity is reported as the slowest rank's."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _dist(backend="nccl"):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group(backend)
         return dist, dist.get_rank(), ws
     return None, 0, 1
 
@@ -212,10 +223,7 @@ def measure(args, mesh, flow, precision, dev, dist, ws, with_e2e):
     if dist:
         dist.barrier()
     total_ms = float(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
-    if dist:
-        t = torch.tensor([total_ms], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = _max_over_ranks(dist, total_ms, f"cuda:{dev}")
     _, st = ctx.iterate(0)
     if st[sid]["state"] != 0 or st[sid]["iters"] != args.warmup + args.steps:
         raise RuntimeError(f"the solve stopped during the timed steps: {st[sid]}")
@@ -235,10 +243,7 @@ def measure(args, mesh, flow, precision, dev, dist, ws, with_e2e):
             ctx.iterate(1)                       # one iteration, per-solve status read back
             ctx.get_fields(sid, out=W_host)      # D2H: the step's result
         e2e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_s], device=f"cuda:{dev}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = _max_over_ranks(dist, e2e_s, f"cuda:{dev}")
         res["e2e"] = {"value": ws * mesh.n_cells * n_e2e / e2e_s, "unit": METRIC,
                       "h2d_bytes_per_step": int(W_host.nbytes), "d2h_bytes_per_step": int(W_host.nbytes) + 48}
     ctx.destroy()
@@ -285,10 +290,7 @@ def measure_batch(args, cases, precision, dev, dist, ws):
                 ktimes.setdefault(name, []).append(t)
             _, st = ctx.iterate(0)
     total_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = _max_over_ranks(dist, total_ms, f"cuda:{dev}")
     states = [q["state"] for q in st]
     res = {"value": ws * sum(live_cells) / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
            "kernel_ms": {k: round(statistics.mean(v), 5) for k, v in ktimes.items()},
@@ -332,7 +334,8 @@ def main():
     ap.add_argument("--impl", default="igks", choices=["igks", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="headline sweep precision (the other one is measured too)")
-    ap.add_argument("--workload", default="turbulent_plate", choices=list(WORKLOADS) + ["naca_batch", "serving"])
+    ap.add_argument("--workload", default="turbulent_plate", choices=list(WORKLOADS) + ["naca_batch", "serving", "cavity"])
+    ap.add_argument("--explicit-cap", type=int, default=1500000, help="cavity: explicit iterations at most")
     ap.add_argument("--requests", type=int, default=16, help="requests of the serving workload")
     ap.add_argument("--cells-lo", type=int, default=2000)
     ap.add_argument("--cells-hi", type=int, default=30000)
@@ -353,6 +356,8 @@ def main():
         return main_batch(args)
     if args.workload == "serving":
         return main_serving(args)
+    if args.workload == "cavity":
+        return main_cavity(args)
     mk, fl_fn, desc = WORKLOADS[args.workload]
     mesh, flow = mk(), fl_fn()
     if args.ordering == "multicolor":
@@ -575,6 +580,49 @@ def main_serving(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+def main_cavity(args):
+    """The paper's cavity (Re 1000, 100 x 100): implicit and explicit scheme from rest to the
+    paper's convergence criterion (Eq. 40 ratio <= 3e-8) on the same kernels -- iterations
+    and device time of each (the comparison of Table 2) -- and the vortex centres of the
+    implicit solution against Table 1."""
+    import torch
+    from paper_1709_00803_gb300 import igks
+    from paper_1709_00803_gb300 import postproc as P
+    dist, rank, ws = _dist()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    n = 100
+    m = G.cavity(n)
+    runs = {}
+    with ClockSampler(dev) as clk:
+        for name, scheme, cap in (("implicit", 0, 40000), ("explicit", 1, args.explicit_cap)):
+            fl = F.cavity_flow(scheme=scheme)
+            fl.eq40_target = 3e-8
+            ctx = igks.Context(precision=1 if scheme == 0 else 0, check_every=1000 if scheme else 100)
+            sid = ctx.mesh_upload(m); ctx.set_flow(sid, fl); ctx.init_freestream(sid)
+            ctx.set_fields(sid, F.rest_state(m, fl))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, st = ctx.iterate(cap)
+            t = time.perf_counter() - t0
+            runs[name] = dict(iterations=st[sid]["iters"], seconds=t, converged=(rc == igks.CONVERGED),
+                              eq40=st[sid]["eq40_ratio"], res_l2_rel=st[sid]["res_l2_rel"],
+                              ms_per_iteration=1e3 * t / max(st[sid]["iters"], 1))
+            if scheme == 0:
+                vort = P.cavity_vortices(ctx.get_fields(sid), n)
+            ctx.destroy()
+    table1 = {"omega": 2.0861, "psi": -0.1178, "x": 0.5335, "y": 0.5681}
+    out = {"metric": "cavity: explicit/implicit time to the Eq. 40 criterion", "unit": "ratio",
+           "value": runs["explicit"]["seconds"] / runs["implicit"]["seconds"] if runs["explicit"]["converged"] else None,
+           "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+           "config": {"workload": "lid-driven cavity, Re 1000, Ma 0.1 sqrt(3), 100 x 100 uniform quads, from rest"},
+           "implicit": runs["implicit"], "explicit": runs["explicit"],
+           "iteration_ratio": runs["explicit"]["iterations"] / runs["implicit"]["iterations"],
+           "paper_table2": {"explicit_iterations": 608000, "implicit_iterations": 4430, "speedup": 64.1},
+           "vortices": vort, "paper_table1_primary": table1, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 if __name__ == "__main__":
     main()

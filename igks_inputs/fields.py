@@ -37,6 +37,7 @@ class Flow:
     c_num: float = 1.0             # numerical collision-time coefficient
     visc_sr: int = 0               # add the viscous spectral radius to lambda_f
     eq40_target: float = 0.0       # if > 0, also stop at the Eq. 40 ratio <= this (paper: 3e-8)
+    scheme: int = 0                # 0 implicit (LU-SGS, Eq. 22), 1 explicit (Eq. 15)
 
     def as_dict(self) -> dict:
         return asdict(self)
@@ -110,4 +111,21 @@ def uniform_state(mesh, flow: Flow) -> np.ndarray:
     W[2] = r0 * v0
     W[3] = p0 / (GAMMA - 1.0) + 0.5 * r0 * (u0 * u0 + v0 * v0)
     W[4] = flow.nut_ratio_inf / flow.reynolds if flow.sa_on else 0.0
+    return W
+
+
+def cavity_flow(scheme: int = 0) -> Flow:
+    """Lid-driven cavity of the paper's first test: Re = 1000 on the lid speed and the
+    cavity size, Ma = 0.1 sqrt(3), laminar; the lid moves with the free-stream velocity
+    (AoA 0: along +x). Implicit CFL from 1000 by Eq. 25 up to 1e6, as the paper reports."""
+    return Flow(mach=0.1 * math.sqrt(3.0), reynolds=1000.0, aoa_deg=0.0, sa_on=0, cfl_init=1000.0,
+                cfl_min=1000.0, cfl_max=1e6, visc_sr=0, limiter=LIMITER_NONE, scheme=scheme)
+
+
+def rest_state(mesh, flow: Flow) -> np.ndarray:
+    """Fluid at rest with the free-stream density and pressure (the cavity's start)."""
+    r0, _, _, p0 = freestream_primitives(flow)
+    W = np.zeros((5, mesh.n_cells))
+    W[0] = r0
+    W[3] = p0 / (GAMMA - 1.0)
     return W

@@ -31,7 +31,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-BC_INTERIOR, BC_FARFIELD, BC_SYMMETRY, BC_WALL, BC_OUTFLOW = 0, 1, 2, 3, 4
+BC_INTERIOR, BC_FARFIELD, BC_SYMMETRY, BC_WALL, BC_OUTFLOW, BC_MOVING_WALL = 0, 1, 2, 3, 4, 5
 
 
 @dataclass
@@ -595,3 +595,17 @@ def serving_specs(n: int = 200, seed: int = 5, cells_lo: int = 2000, cells_hi: i
             m=float(rng.uniform(0.0, 0.06)), p=float(rng.uniform(0.2, 0.6)), t=float(rng.uniform(0.08, 0.18)),
             gap=float(rng.exponential(1.0)), mesh_seed=1000 * seed + i))
     return out
+
+
+def cavity(n: int = 100) -> Mesh:
+    """Lid-driven cavity: n x n uniform quads on the unit square, fixed non-slip walls on
+    the bottom and sides, the top a wall moving with the free-stream velocity (the lid)."""
+    xs = np.linspace(0.0, 1.0, n + 1)
+    X, Y = np.meshgrid(xs, xs)
+    xy = np.stack([X.ravel(), Y.ravel()], axis=1)
+    nid = lambda i, j: j * (n + 1) + i
+    cells = [[nid(i, j), nid(i + 1, j), nid(i + 1, j + 1), nid(i, j + 1)] for j in range(n) for i in range(n)]
+    m = build_mesh(xy, cells, lambda a, b, xm, ym: BC_MOVING_WALL if abs(ym - 1.0) < 1e-12 else BC_WALL,
+                   name=f"cavity_{n}x{n}")
+    m.meta = dict(kind="cavity", n=n)
+    return m

@@ -50,6 +50,12 @@ extern "C" {
 #define IGKS_BC_WALL 3      /* adiabatic non-slip wall */
 #define IGKS_BC_OUTFLOW 4   /* outflow: boundary-normal velocity from the Riemann invariants,
                                density, tangential velocity, temperature and nu_tilde from inside */
+#define IGKS_BC_MOVING_WALL 5 /* adiabatic non-slip wall moving with the tangential part of the
+                               free-stream velocity (a lid) */
+
+/* time marching of a solve */
+#define IGKS_SCHEME_IMPLICIT 0  /* LU-SGS sweeps (Eq. 22) with the implicit CFL (Eq. 24-25) */
+#define IGKS_SCHEME_EXPLICIT 1  /* explicit gas-kinetic scheme, Eq. 15: W += dt M / Omega */
 
 /* precision of the LU-SGS sweeps; flux, residual and state update are always FP64 */
 #define IGKS_PREC_FP64 0
@@ -87,7 +93,7 @@ typedef struct igks_flow {
   double venkat_k;         /* Venkatakrishnan limiter constant */
   double c_num;            /* numerical collision time coefficient (pressure-jump term) */
   int32_t visc_sr;         /* add the viscous term to the face spectral radius */
-  int32_t pad_;
+  int32_t scheme;          /* IGKS_SCHEME_IMPLICIT (LU-SGS) or IGKS_SCHEME_EXPLICIT (Eq. 15) */
   double eq40_target;      /* if > 0, also stop when the Eq. 40 ratio of an update is <= it */
 } igks_flow;
 

@@ -33,7 +33,7 @@ class OraFlow(C.Structure):
                 ("nut_ratio_inf", C.c_double), ("cfl_exp", C.c_double), ("cfl_init", C.c_double),
                 ("cfl_min", C.c_double), ("cfl_max", C.c_double), ("res_target", C.c_double),
                 ("venkat_k", C.c_double), ("c_num", C.c_double),
-                ("visc_sr", C.c_int), ("pad_", C.c_int), ("eq40_target", C.c_double)]
+                ("visc_sr", C.c_int), ("scheme", C.c_int), ("eq40_target", C.c_double)]
 
 
 def build(force: bool = False) -> str:

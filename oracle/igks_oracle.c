@@ -592,7 +592,7 @@ ora_solver* ora_create(int n_nodes, const double* xy, int n_cells, const int* ce
   for (int i = 0; i < n_cells; i++) {
     double dmin = 1e300;
     for (int f = 0; f < n_faces; f++) {
-      if (face_bc[f] != 3) continue;
+      if (face_bc[f] != 3 && face_bc[f] != 5) continue;
       int a = face_nodes[2 * f], b = face_nodes[2 * f + 1];
       double d = seg_dist(s->cx[i], s->cy[i], xy[2 * a], xy[2 * a + 1], xy[2 * b], xy[2 * b + 1]);
       if (d < dmin) dmin = d;
@@ -653,6 +653,18 @@ static void ghost_state(const ora_solver* s, int f, const double* Wi, double* Wg
   int bc = s->face_bc[f];
   if (bc == 3) {                /* non-slip wall: momentum and nu_tilde change sign */
     Wg[0] = Wi[0]; Wg[1] = -Wi[1]; Wg[2] = -Wi[2]; Wg[3] = Wi[3]; Wg[4] = -Wi[4];
+  } else if (bc == 5) {         /* non-slip wall moving with the tangential part of the free-stream
+                                   velocity: the ghost velocity mirrors the inside one about the
+                                   wall velocity, same density and internal energy, nu_tilde sign */
+    double Wf[5];
+    freestream(&s->flow, Wf);
+    double tx = -ny, ty = nx;
+    double uw = (Wf[1] * tx + Wf[2] * ty) / Wf[0];
+    double r = Wi[0], u = Wi[1] / r, v = Wi[2] / r;
+    double ug = 2.0 * uw * tx - u, vg = 2.0 * uw * ty - v;
+    Wg[0] = r; Wg[1] = r * ug; Wg[2] = r * vg;
+    Wg[3] = Wi[3] - 0.5 * r * (u * u + v * v) + 0.5 * r * (ug * ug + vg * vg);
+    Wg[4] = -Wi[4];
   } else if (bc == 2) {         /* symmetry: normal momentum changes sign */
     double mn = Wi[1] * nx + Wi[2] * ny;
     Wg[0] = Wi[0]; Wg[1] = Wi[1] - 2.0 * mn * nx; Wg[2] = Wi[2] - 2.0 * mn * ny; Wg[3] = Wi[3]; Wg[4] = Wi[4];
@@ -685,7 +697,7 @@ static void ghost_state(const ora_solver* s, int f, const double* Wi, double* Wg
 static void ghost_increment(const ora_solver* s, int f, const double* dWi, double* dWg) {
   double nx = s->fnx[f], ny = s->fny[f];
   int bc = s->face_bc[f];
-  if (bc == 3) {
+  if (bc == 3 || bc == 5) {   /* walls (a moving wall maps increments like a fixed one) */
     dWg[0] = dWi[0]; dWg[1] = -dWi[1]; dWg[2] = -dWi[2]; dWg[3] = dWi[3]; dWg[4] = -dWi[4];
   } else if (bc == 2) {
     double mn = dWi[1] * nx + dWi[2] * ny;
@@ -847,14 +859,24 @@ static int step_fluxes(ora_solver* s) {
       to_face(sRn, nx, ny, SRn);
       to_face(sRt, nx, ny, SRt);
       dR = -(dxr * nx + dyr * ny);
-    } else if (bc == 2 || bc == 3) {
+    } else if (bc == 2 || bc == 3 || bc == 5) {
       /* mirror image of the left side: state mapped by the boundary condition, the
-       * normal slope also reflected */
+       * normal slope also reflected; a moving wall mirrors the tangential velocity about
+       * the wall velocity (slopes map as at a fixed wall) */
       double tmp[4];
-      face_bc_map(bc, WL, WR);
-      face_bc_map(bc, SLn, tmp);
+      int sb = bc == 5 ? 3 : bc;
+      face_bc_map(sb, WL, WR);
+      if (bc == 5) {
+        double Wf[5];
+        freestream(fl, Wf);
+        double uw = (Wf[1] * tx + Wf[2] * ty) / Wf[0];
+        double r = WL[0], ut = WL[2] / r, utg = 2.0 * uw - ut;
+        WR[2] = r * utg;
+        WR[3] = WL[3] - 0.5 * r * ut * ut + 0.5 * r * utg * utg;
+      }
+      face_bc_map(sb, SLn, tmp);
       for (int v = 0; v < 4; v++) SRn[v] = -tmp[v];
-      face_bc_map(bc, SLt, SRt);
+      face_bc_map(sb, SLt, SRt);
       dR = dL;
     } else {
       /* free stream and outflow: the ghost state, without slopes */
@@ -1067,6 +1089,14 @@ static void step_sweeps(ora_solver* s) {
   free(Dsa);
 }
 
+/* explicit scheme (Eq. 15, written as Eq. 16): W^{n+1} = W^n + dt M / Omega */
+static void step_explicit(ora_solver* s) {
+  for (int i = 0; i < s->n_cells; i++) {
+    for (int v = 0; v < 4; v++) s->dW[5 * i + v] = s->dt * s->M[5 * i + v] / s->area[i];
+    s->dW[5 * i + 4] = s->flow.sa_on ? s->dt * s->M[5 * i + 4] / s->area[i] : 0.0;
+  }
+}
+
 static void step_update(ora_solver* s) {
   double eq40 = 0.0;
   int bad = 0;
@@ -1095,7 +1125,8 @@ int ora_iterate(ora_solver* s, int n_iter) {
     if (step_fluxes(s)) { s->status = -5; return s->status; }
     step_residual(s);
     step_norms(s);
-    step_sweeps(s);
+    if (s->flow.scheme == 1) step_explicit(s);
+    else step_sweeps(s);
     step_update(s);
     s->iter++;
     if (s->status < 0) return s->status;

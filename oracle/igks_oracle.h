@@ -20,7 +20,7 @@ typedef struct ora_flow {
   double nut_ratio_inf, cfl_exp, cfl_init, cfl_min, cfl_max, res_target;
   double venkat_k, c_num;
   int visc_sr;
-  int pad_;
+  int scheme;           /* 0: implicit, LU-SGS (Eq. 22); 1: explicit (Eq. 16) */
   double eq40_target;   /* if > 0: also converged when the Eq. 40 ratio is <= it */
 } ora_flow;
 

@@ -115,7 +115,7 @@ static DevFlow make_devflow(const igks_flow& f) {
   d.cfl_exp = f.cfl_exp; d.cfl_init = f.cfl_init; d.cfl_min = f.cfl_min; d.cfl_max = f.cfl_max;
   d.res_target = f.res_target; d.venkat_k = f.venkat_k; d.c_num = f.c_num;
   d.eq40_target = f.eq40_target;
-  d.sa_on = f.sa_on; d.limiter = f.limiter; d.visc_sr = f.visc_sr;
+  d.sa_on = f.sa_on; d.limiter = f.limiter; d.visc_sr = f.visc_sr; d.scheme = f.scheme;
   return d;
 }
 
@@ -276,7 +276,7 @@ static int build(igks_ctx* ctx) {
       fnode[g] = no + m.face_nodes[2 * f];
       fnode[nf + g] = no + m.face_nodes[2 * f + 1];
       if (fR[g] < 0) bface.push_back(g);
-      if (fR[g] < 0 && fbc[g] == IGKS_BC_WALL) wall_face.push_back(g);
+      if (fR[g] < 0 && (fbc[g] == IGKS_BC_WALL || fbc[g] == IGKS_BC_MOVING_WALL)) wall_face.push_back(g);
     }
     wall_ptr[s + 1] = (int)wall_face.size();
     // sweep schedule
@@ -318,7 +318,8 @@ static int build(igks_ctx* ctx) {
             const int l_ = m.face_cells[2 * f], r_ = m.face_cells[2 * f + 1];
             const int kg = cf_ptr[co + i] + (k - lp[i]);
             if (r_ < 0) {
-              if (!fwd && (m.face_bc[f] == IGKS_BC_WALL || m.face_bc[f] == IGKS_BC_SYMMETRY)) {
+              if (!fwd && (m.face_bc[f] == IGKS_BC_WALL || m.face_bc[f] == IGKS_BC_SYMMETRY ||
+                           m.face_bc[f] == IGKS_BC_MOVING_WALL)) {
                 map[kg] = (int)sj.size();
                 sj.push_back(-1 - (fo + f));
                 sslot.push_back(-1);
@@ -574,7 +575,7 @@ int igks_check_mesh_(int32_t n_nodes, const double* xy, int32_t n_cells, const i
     if (a < 0 || a >= n_nodes || b < 0 || b >= n_nodes || a == b) return fail(IGKS_EMESH, "face node index out of range");
     if (l < 0 || l >= n_cells) return fail(IGKS_EMESH, "face without a valid left cell");
     if (r >= n_cells || r == l) return fail(IGKS_EMESH, "face right cell out of range");
-    if (r < 0 && (face_bc[f] < IGKS_BC_FARFIELD || face_bc[f] > IGKS_BC_OUTFLOW))
+    if (r < 0 && (face_bc[f] < IGKS_BC_FARFIELD || face_bc[f] > IGKS_BC_MOVING_WALL))
       return fail(IGKS_EMESH, "boundary face without a boundary tag");
     if (r >= 0 && face_bc[f] != IGKS_BC_INTERIOR) return fail(IGKS_EMESH, "interior face with a boundary tag");
     deg[l]++;
@@ -603,7 +604,7 @@ int igks_check_mesh_(int32_t n_nodes, const double* xy, int32_t n_cells, const i
 bool igks_check_flow_(const igks_flow* f) {
   return f->mach > 0 && f->reynolds > 0 && f->prandtl > 0 && f->cfl_exp > 0 && f->cfl_init > 0 &&
          f->cfl_min > 0 && f->cfl_max >= f->cfl_min && f->limiter >= 0 && f->limiter <= 2 && f->t_ref > 0 &&
-         f->eq40_target >= 0;
+         f->eq40_target >= 0 && (f->scheme == IGKS_SCHEME_IMPLICIT || f->scheme == IGKS_SCHEME_EXPLICIT);
 }
 
 extern "C" {

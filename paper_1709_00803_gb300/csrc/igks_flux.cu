@@ -211,9 +211,15 @@ __global__ void __launch_bounds__(128) k_flux(Dev d) {
     for (int v = 0; v < 5; v++) WcRg[v] = d.G[v * nf + f];
     muR = d.Gmu[f];
     mtR = d.Gmu[nf + f];
-    if (bc == 2 || bc == 3) {
-      const double st2 = (bc == 3) ? -1.0 : 1.0;
+    if (bc == 2 || bc == 3 || bc == 5) {
+      const double st2 = (bc == 2) ? 1.0 : -1.0;
       WR[0] = WL[0]; WR[1] = -WL[1]; WR[2] = st2 * WL[2]; WR[3] = WL[3];
+      if (bc == 5) {   // moving wall: tangential velocity mirrored about the wall velocity
+        const double uw = (fl.Winf[1] * tx + fl.Winf[2] * ty) / fl.Winf[0];
+        const double ut = WL[2] / WL[0], utg = 2.0 * uw - ut;
+        WR[2] = WL[0] * utg;
+        WR[3] = WL[3] - 0.5 * WL[0] * ut * ut + 0.5 * WL[0] * utg * utg;
+      }
       SRn[0] = -SLn[0]; SRn[1] = SLn[1]; SRn[2] = -st2 * SLn[2]; SRn[3] = -SLn[3];
       SRt[0] = SLt[0]; SRt[1] = -SLt[1]; SRt[2] = st2 * SLt[2]; SRt[3] = SLt[3];
     } else {

@@ -35,6 +35,17 @@ __device__ inline void ghost_state(const DevFlow& fl, int bc, double nx, double 
     Wg[0] = Wi[0]; Wg[1] = -Wi[1]; Wg[2] = -Wi[2]; Wg[3] = Wi[3]; Wg[4] = -Wi[4];
     return;
   }
+  if (bc == 5) {          // moving wall: velocity mirrored about the wall velocity
+    const double* Wf = fl.Winf;
+    const double tx = -ny, ty = nx;
+    const double uw = (Wf[1] * tx + Wf[2] * ty) / Wf[0];
+    const double r = Wi[0], u = Wi[1] / r, v = Wi[2] / r;
+    const double ug = 2.0 * uw * tx - u, vg = 2.0 * uw * ty - v;
+    Wg[0] = r; Wg[1] = r * ug; Wg[2] = r * vg;
+    Wg[3] = Wi[3] - 0.5 * r * (u * u + v * v) + 0.5 * r * (ug * ug + vg * vg);
+    Wg[4] = -Wi[4];
+    return;
+  }
   if (bc == 2) {          // symmetry: normal momentum reversed
     double mn = Wi[1] * nx + Wi[2] * ny;
     Wg[0] = Wi[0]; Wg[1] = Wi[1] - 2.0 * mn * nx; Wg[2] = Wi[2] - 2.0 * mn * ny;

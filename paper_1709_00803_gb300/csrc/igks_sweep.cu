@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_sweep_prep(Dev d) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.nc_pad) return;
   const int s = d.cell_solve[i];
-  if (s < 0 || d.st[s].state != 0) return;
+  if (s < 0 || d.st[s].state != 0 || d.flow[s].scheme == 1) return;   // explicit solves: no sweeps
   const DevFlow& fl = d.flow[s];
   const int n = d.nc_pad, nf = d.nf;
   const double cfl = d.st[s].cfl;
@@ -229,15 +229,19 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_update(Dev d) {
     double Wi[5];
 #pragma unroll
     for (int v = 0; v < 5; v++) Wi[v] = d.W[v * n + i];
+    const int si = d.cell_solve[i];
+    const bool expl = d.flow[si].scheme == 1;
+    // explicit scheme (Eq. 15 as Eq. 16): dW = dt M / Omega, in FP64
+    const double xf = expl ? __longlong_as_double((long long)d.dt_bits[si]) / d.area[i] : 0.0;
     double num = 0.0, den = 0.0;
 #pragma unroll
     for (int v = 0; v < 4; v++) {
-      const double dv = (double)dWo[v * n + i];
+      const double dv = expl ? xf * d.M[v * n + i] : (double)dWo[v * n + i];
       num += dv * dv;
       den += Wi[v] * Wi[v];
       Wi[v] += dv;
     }
-    Wi[4] += (double)dWo[4 * n + i];
+    Wi[4] += expl ? (d.flow[si].sa_on ? xf * d.M[4 * n + i] : 0.0) : (double)dWo[4 * n + i];
     if (Wi[4] < 0.0) Wi[4] = 0.0;
     eq40 = sqrt(num) / sqrt(den);
     const double p = pressure_of(Wi[0], Wi[1], Wi[2], Wi[3]);
@@ -429,7 +433,7 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_sweep_fwd_narrow(Dev d) {
   FwdRec<T>* stage = (FwdRec<T>*)(smem_raw + (size_t)13 * RING * sizeof(T));
   FwdRec<T>* st = stage + threadIdx.x;               // staged record of this thread's next position
   const int s = blockIdx.x;
-  if (d.st[s].state != 0) return;
+  if (d.st[s].state != 0 || d.flow[s].scheme == 1) return;
   const bool sa_on = d.flow[s].sa_on;
   const int l0 = d.lvl_solve_ptr[s], l1 = d.lvl_solve_ptr[s + 1] - 1;
   const int pbase = d.fwd_lvl[l0];
@@ -525,7 +529,7 @@ __device__ __forceinline__ void bwd_entry(const Dev& d, const T* ring, const T* 
   } else {
     const int nf = d.nf, fc = -1 - j;
     w[0] = ws[0]; w[3] = ws[3];
-    if (d.fbc[fc] == 3) { w[1] = -ws[1]; w[2] = -ws[2]; w[4] = -ws[4]; }
+    if (d.fbc[fc] == 3 || d.fbc[fc] == 5) { w[1] = -ws[1]; w[2] = -ws[2]; w[4] = -ws[4]; }
     else {
       const T fx = (T)d.fnx[fc], fy = (T)d.fny[fc];
       const T mn = ws[1] * fx + ws[2] * fy;
@@ -584,7 +588,7 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_sweep_bwd_narrow(Dev d) {
   BwdRec<T>* stage = (BwdRec<T>*)(smem_raw + (size_t)13 * RING * sizeof(T));
   BwdRec<T>* st = stage + threadIdx.x;
   const int s = blockIdx.x;
-  if (d.st[s].state != 0) return;
+  if (d.st[s].state != 0 || d.flow[s].scheme == 1) return;
   const bool sa_on = d.flow[s].sa_on;
   const int l0 = d.blvl_solve_ptr[s], l1 = d.blvl_solve_ptr[s + 1] - 1;
   const int pbase = d.bwd_lvl[l0];
@@ -618,7 +622,7 @@ __global__ void k_sweep_fwd_level(Dev d, int b, int e) {
   if (k >= e) return;
   const int i = d.wfwd_cells[k];
   const int s = d.cell_solve[i];
-  if (d.st[s].state != 0) return;
+  if (d.st[s].state != 0 || d.flow[s].scheme == 1) return;
   fwd_cell<T>(d, i, d.flow[s].sa_on);
 }
 
@@ -628,7 +632,7 @@ __global__ void k_sweep_bwd_level(Dev d, int b, int e) {
   if (k >= e) return;
   const int i = d.wbwd_cells[k];
   const int s = d.cell_solve[i];
-  if (d.st[s].state != 0) return;
+  if (d.st[s].state != 0 || d.flow[s].scheme == 1) return;
   bwd_cell<T>(d, i, d.flow[s].sa_on);
 }
 

@@ -36,7 +36,7 @@ class Flow(C.Structure):
                 ("sa_on", C.c_int32), ("limiter", C.c_int32), ("nut_ratio_inf", C.c_double),
                 ("cfl_exp", C.c_double), ("cfl_init", C.c_double), ("cfl_min", C.c_double),
                 ("cfl_max", C.c_double), ("res_target", C.c_double), ("venkat_k", C.c_double),
-                ("c_num", C.c_double), ("visc_sr", C.c_int32), ("pad_", C.c_int32),
+                ("c_num", C.c_double), ("visc_sr", C.c_int32), ("scheme", C.c_int32),
                 ("eq40_target", C.c_double)]
 
 

@@ -233,3 +233,27 @@ def test_autotune_leaves_iterates_unchanged():
         ctx.destroy()
     for a, b in zip(*results):
         assert np.array_equal(a, b)
+
+
+def test_moving_wall_cavity_one_iteration():
+    m = G.cavity(40)
+    fl = F.cavity_flow()
+    ctx, sid, ora = make_pair(m, fl, seeded(m, fl, 21, amp=0.05))
+    ctx.iterate(1); ora.iterate(1)
+    _compare_iteration(ctx, sid, ora)
+
+
+@pytest.mark.parametrize("mk,flow_fn", [(lambda: G.cavity(40), lambda: F.cavity_flow(scheme=1)),
+                                        (lambda: G.flat_plate_hybrid(nx=48, nq=16, ntri_rows=12, first=1e-5, seed=3),
+                                         F.turbulent_plate_flow)])
+def test_explicit_scheme_matches_oracle(mk, flow_fn):
+    """The explicit gas-kinetic scheme (Eq. 15) on the same kernels: no sweeps, W += dt M / Omega."""
+    m = mk()
+    fl = flow_fn()
+    fl.scheme = 1
+    for precision in (0, 1):    # the sweep precision plays no part in the explicit update
+        ctx, sid, ora = make_pair(m, fl, seeded(m, fl, 22, amp=0.05), precision=precision)
+        ctx.iterate(1); ora.iterate(1)
+        _compare_iteration(ctx, sid, ora, skip=("dwstar", "dw"))
+        ctx.iterate(6); ora.iterate(6)
+        assert_close("W after 7 explicit steps", ctx.get_fields(sid), ora.get(O.ORA_W), TOL)

@@ -337,3 +337,57 @@ def test_outflow_ghost_passes_inside_values_and_averages_the_invariants():
         m3, gh3 = ghosts(p=base["p"] * (1 + eps) ** 2)
         un3 = (gh3[1, f] * n[0] + gh3[2, f] * n[1]) / gh3[0, f]
         assert abs((un3 - un0) / (c0 * eps) - 1.0 / (g - 1.0)) < 1e-5
+
+
+def test_explicit_scheme_conserves_mass_and_energy_in_a_closed_mirror_box():
+    """Eq. 15 is in flux form: on a box closed by symmetry planes (an exact mirror of the
+    kinetic problem, so no mass or energy crosses them) total mass and energy stay fixed
+    to round-off, step after step."""
+    from igks_inputs import meshgen as G
+    m = G.tiny_quads(6, 5, skew=0.3, seed=2, bcs=("symmetry", "symmetry"))
+    fl = F.cavity_flow(scheme=1)
+    o = O.Oracle(m, fl)
+    W0 = F.perturbed_state(m, fl, seed=4, amp=0.05)
+    o.set_W(W0)
+    area = None
+    for _ in range(4):
+        assert o.iterate(1) == 0
+        W = o.get(O.ORA_W)
+        area = o.get(O.ORA_GEOM_CELL)[0]
+        for v in (0, 3):
+            tot0 = (W0[v] * area).sum()
+            assert abs((W[v] * area).sum() - tot0) <= 1e-14 * abs(tot0)
+    # and it is not a fixed point: the fields did change
+    assert np.abs(W - W0).max() > 1e-6
+
+
+def test_explicit_step_of_a_uniform_state_is_zero():
+    from igks_inputs import meshgen as G
+    m = G.tiny_quads(3, 3, bcs=("symmetry", "farfield"))
+    fl = F.laminar_plate_flow(); fl.scheme = 1
+    o = O.Oracle(m, fl)
+    W0 = F.uniform_state(m, fl)
+    o.set_W(W0)
+    o.iterate(2)
+    np.testing.assert_allclose(o.get(O.ORA_W), W0, rtol=1e-13, atol=1e-13)
+
+
+def test_moving_wall_ghost_mirrors_velocity_about_the_lid():
+    """A fluid moving with the lid sees itself as the ghost (no slip); a fluid at rest sees
+    a ghost at twice the lid velocity; density and internal energy are those inside."""
+    from igks_inputs import meshgen as G
+    m = G.cavity(3)
+    fl = F.cavity_flow()
+    p0 = 1.0 / (F.GAMMA * fl.mach ** 2)
+    lid = np.nonzero(m.face_bc == G.BC_MOVING_WALL)[0]
+    for u_in, u_ghost in ((1.0, 1.0), (0.0, 2.0), (0.4, 1.6)):
+        W = np.repeat(np.array(_conserved(1.05, u_in, 0.0, 1.02 * p0))[:, None], m.n_cells, axis=1)
+        o = O.Oracle(m, fl)
+        o.set_W(W)
+        o.iterate(1)
+        gh = o.get(O.ORA_GHOST)[:, lid]
+        r, u, v, p = _prim(gh)
+        np.testing.assert_allclose(r, 1.05, rtol=1e-15)
+        np.testing.assert_allclose(u, u_ghost, rtol=1e-14, atol=1e-14)
+        np.testing.assert_allclose(v, 0.0, atol=1e-14)
+        np.testing.assert_allclose(p, 1.02 * p0, rtol=1e-13)
