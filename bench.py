@@ -47,8 +47,11 @@ SM_COUNT, SM_MAX_GHZ = 152, 2.07
 # nominal) x 2 flop x 152 SMs x 2.07 GHz
 FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_GHZ / 1e3
 # Executed FP64 flops per face of k_flux (2 x DFMA + DADD + DMUL from ncu on the turbulent
-# plate, 35056 faces): the per-unit figure of its ALU roofline
-FLUX_FLOPS_PER_FACE = 3556.0
+# plate, 35056 faces, profiles/k_flux_turbulent_plate.md): the per-unit figure of its ALU
+# roofline
+FLUX_FLOPS_PER_FACE = 3122.0
+# DRAM bytes (read + write) per face of one k_flux launch, from the same capture
+FLUX_DRAM_BYTES_PER_FACE = 188.1
 
 
 def alg_bytes(kernel, t, nc, nf):
@@ -230,6 +233,7 @@ def measure(args, mesh, flow, precision, dev, dist, ws, with_e2e):
     res = {"value": ws * mesh.n_cells * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
            "kernel_ms": {k: round(statistics.mean(v), 5) for k, v in ktimes.items()},
            "launches_per_step": ctx.launches_per_iteration(), "clocks": clk.summary(), "info": info,
+           "levels": (info["levels_fwd"], info["levels_bwd"]),
            "solver_state": {"iters": st[sid]["iters"], "res_l2_rel": st[sid]["res_l2_rel"], "cfl": st[sid]["cfl"]}}
     if with_e2e:
         W_host = torch.empty((5, mesh.n_cells), dtype=torch.float64).pin_memory().numpy()
@@ -317,13 +321,38 @@ def rooflines(res, mesh, precision):
     flux_t = km["k_flux"]
     ach_f = FLUX_FLOPS_PER_FACE * mesh.n_faces / (flux_t / 1e3) / 1e12
     flux = {"bound": "alu", "kernel": "k_flux", "achieved": ach_f, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach_f / FP64_PEAK_TFLOPS, "traffic": 6617344 * mesh.n_faces / 35056,
+            "frac": ach_f / FP64_PEAK_TFLOPS,
+            "traffic": FLUX_DRAM_BYTES_PER_FACE * mesh.n_faces if FLUX_DRAM_BYTES_PER_FACE else None,
             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
             "flops_per_face": FLUX_FLOPS_PER_FACE}
     if dom == "k_flux":
         # the flux kernel is bound by the FP64 pipe, not by memory: report that roofline
         dominant = dict(flux, alg_bytes_per_launch=b, hbm_achieved_gbs=ach, hbm_frac=ach / hbm)
     return dominant, flux
+
+
+def per_kernel(res, mesh, precision):
+    """Every kernel of the iteration against the roofline that bounds it: algorithmic bytes
+    (HBM) or FP64 flops (the flux) per launch over its event-timed duration; the sweeps
+    also per dependency level (their bound is the depth of the sweep order)."""
+    peaks, _ = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    t = 4 if precision == "mixed" else 8
+    out = {}
+    for k, ms in res["kernel_ms"].items():
+        row = {"ms": ms}
+        b = alg_bytes(k, t, mesh.n_cells, mesh.n_faces)
+        if b:
+            row.update(alg_bytes=b, gbs=b / (ms / 1e3) / 1e9, hbm_frac=b / (ms / 1e3) / 1e9 / hbm)
+        if k == "k_flux":
+            tf = FLUX_FLOPS_PER_FACE * mesh.n_faces / (ms / 1e3) / 1e12
+            row.update(fp64_tflops=tf, fp64_frac=tf / FP64_PEAK_TFLOPS)
+        lv = res.get("levels")
+        if lv and k in ("k_sweep_fwd", "k_sweep_bwd"):
+            n = lv[0] if k == "k_sweep_fwd" else lv[1]
+            row.update(levels=n, us_per_level=1e3 * ms / n)
+        out[k] = row
+    return out
 
 
 def main():
@@ -388,6 +417,7 @@ def main():
                       "l2": "flushed between steps (256 MiB write outside the timed intervals)"},
            "e2e": head["e2e"], "gpu_launches": head["launches_per_step"] * args.steps,
            "kernel_ms": head["kernel_ms"], "roofline": dominant, "roofline_flux": flux_roof,
+           "per_kernel": per_kernel(head, mesh, args.precision),
            "clocks": head["clocks"], "solver_state": head["solver_state"]}
     if other:
         out["other"] = {"precision": other_p, "value": other["value"], "ms_per_step": other["ms_per_step"],
@@ -438,6 +468,7 @@ def main_batch(args):
                       "l2": "flushed between steps (256 MiB write outside the timed intervals)"},
            "gpu_launches": head["launches_per_step"] * args.steps, "kernel_ms": head["kernel_ms"],
            "roofline": dominant, "roofline_flux": flux_roof, "clocks": head["clocks"],
+           "per_kernel": per_kernel(head, tot, precision),
            "batch": {k: head[k] for k in ("solves", "running", "converged", "diverged", "live_cells_first_last",
                                           "autotune")}}
     if rank == 0:

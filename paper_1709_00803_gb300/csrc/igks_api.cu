@@ -115,6 +115,7 @@ static DevFlow make_devflow(const igks_flow& f) {
   d.cfl_exp = f.cfl_exp; d.cfl_init = f.cfl_init; d.cfl_min = f.cfl_min; d.cfl_max = f.cfl_max;
   d.res_target = f.res_target; d.venkat_k = f.venkat_k; d.c_num = f.c_num;
   d.eq40_target = f.eq40_target;
+  d.pr_fix = 1.0 / f.prandtl - 1.0;
   d.sa_on = f.sa_on; d.limiter = f.limiter; d.visc_sr = f.visc_sr; d.scheme = f.scheme;
   return d;
 }

@@ -26,6 +26,7 @@ struct DevFlow {
   double mach, re, prandtl, s_star, lam_inf, mu_inf, nut_inf, p_inf;
   double Winf[5];
   double cfl_exp, cfl_init, cfl_min, cfl_max, res_target, venkat_k, c_num, eq40_target;
+  double pr_fix;   // 1/Pr - 1, the factor of the Prandtl-number fix
   int sa_on, limiter, visc_sr, scheme;
 };
 

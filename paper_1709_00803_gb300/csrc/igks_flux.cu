@@ -29,14 +29,34 @@ __device__ __forceinline__ void moments_full(double U, double h, double* m) {   
   for (int k = 0; k + 2 < N; k++) m[k + 2] = U * m[k + 1] + (k + 1) * h * m[k];
 }
 
+// the recurrence of the u-moments from <u^0> and <u^1>
+template <int N>
+__device__ __forceinline__ void moments_rec(double U, double h, double* m) {
+#pragma unroll
+  for (int k = 0; k + 2 < N; k++) m[k + 2] = U * m[k + 1] + (k + 1) * h * m[k];
+}
+
 // u-moments over u >= 0 (sgn = +1) or u < 0 (sgn = -1)
 template <int N>
 __device__ __forceinline__ void moments_half(double U, double lam, double h, double sgn, double* m) {
-  double sl = sqrt(lam);
-  m[0] = 0.5 * erfc(-sgn * sl * U);
-  m[1] = U * m[0] + sgn * 0.5 * exp(-lam * U * U) * RSQRT_PI / sl;
-#pragma unroll
-  for (int k = 0; k + 2 < N; k++) m[k + 2] = U * m[k + 1] + (k + 1) * h * m[k];
+  const double isl = rsqrt(lam);
+  m[0] = 0.5 * erfc(-sgn * (lam * isl) * U);
+  m[1] = U * m[0] + sgn * 0.5 * exp(-lam * U * U) * RSQRT_PI * isl;
+  moments_rec<N>(U, h, m);
+}
+
+// both half-space u-moment tables of one Maxwellian: <u^0>_{u<0} = 1 - <u^0>_{u>=0}
+// (erfc(x) + erfc(-x) = 2), and the exponential term is shared
+template <int N>
+__device__ __forceinline__ void moments_half_pair(double U, double lam, double h, double* mp, double* mn) {
+  const double isl = rsqrt(lam);
+  const double e = 0.5 * exp(-lam * U * U) * RSQRT_PI * isl;
+  mp[0] = 0.5 * erfc(-(lam * isl) * U);
+  mn[0] = 1.0 - mp[0];
+  mp[1] = U * mp[0] + e;
+  mn[1] = U * mn[0] - e;
+  moments_rec<N>(U, h, mp);
+  moments_rec<N>(U, h, mn);
 }
 
 // <u^A v^B psi>, psi = (1, u, v, (u^2+v^2+xi^2)/2)
@@ -74,16 +94,30 @@ __device__ __forceinline__ void mauv(const double* u, const double* v, double x2
   for (int k = 0; k < 4; k++) acc[k] += s * (r[k] + 0.5 * a[3] * h[k]);
 }
 
-// closed-form solution of <a psi>_g = b for a Maxwellian (U, V, lambda), K internal dof
-__device__ __forceinline__ void solve_moment(double U, double V, double lam, const double* b, double* a) {
-  double E2 = U * U + V * V + (KDOF + 2) / (2.0 * lam);
-  double R4 = 2.0 * b[3] - E2 * b[0];
-  double R2 = b[1] - U * b[0];
-  double R3 = b[2] - V * b[0];
-  a[3] = 4.0 * lam * lam / (KDOF + 2) * (R4 - 2.0 * U * R2 - 2.0 * V * R3);
-  a[2] = 2.0 * lam * R3 - V * a[3];
-  a[1] = 2.0 * lam * R2 - U * a[3];
-  a[0] = b[0] - U * a[1] - V * a[2] - 0.5 * a[3] * E2;
+// the constants of the closed-form moment solve of one Maxwellian (U, V, lambda), computed
+// once and shared by all the solves about it (no division inside a solve)
+struct MSolve {
+  double U, V, E2, l2, c4;   // E2 = U^2 + V^2 + (K+2)/(2 lambda), l2 = 2 lambda, c4 = 4 lambda^2/(K+2)
+};
+
+__device__ __forceinline__ MSolve msolve(double U, double V, double lam, double h) {   // h = 1/(2 lambda)
+  MSolve m;
+  m.U = U; m.V = V;
+  m.E2 = U * U + V * V + (KDOF + 2) * h;
+  m.l2 = 2.0 * lam;
+  m.c4 = (4.0 / (KDOF + 2)) * lam * lam;
+  return m;
+}
+
+// closed-form solution of <a psi>_g = b for the Maxwellian of m, K internal dof
+__device__ __forceinline__ void solve_moment(const MSolve& m, const double* b, double* a) {
+  double R4 = 2.0 * b[3] - m.E2 * b[0];
+  double R2 = b[1] - m.U * b[0];
+  double R3 = b[2] - m.V * b[0];
+  a[3] = m.c4 * (R4 - 2.0 * m.U * R2 - 2.0 * m.V * R3);
+  a[2] = m.l2 * R3 - m.V * a[3];
+  a[1] = m.l2 * R2 - m.U * a[3];
+  a[0] = b[0] - m.U * a[1] - m.V * a[2] - 0.5 * a[3] * m.E2;
 }
 
 __device__ __forceinline__ void prim(const double* W, double* r, double* U, double* V, double* lam) {
@@ -120,18 +154,19 @@ __device__ __forceinline__ void side_terms(const double* Wf, const double* sn, c
   // spatial slopes of Eq. 101 and the time slope of Eq. 11
   double an[4], at[4], A[4], b[4];
   const double ir = 1.0 / r;
+  const MSolve ms = msolve(U, V, lam, h);
 #pragma unroll
   for (int k = 0; k < 4; k++) b[k] = sn[k] * ir;
-  solve_moment(U, V, lam, b, an);
+  solve_moment(ms, b, an);
 #pragma unroll
   for (int k = 0; k < 4; k++) b[k] = st[k] * ir;
-  solve_moment(U, V, lam, b, at);
+  solve_moment(ms, b, at);
   double m[4] = {0, 0, 0, 0};
   mauv<1, 0>(u, v, x2, x4, an, 1.0, m);
   mauv<0, 1>(u, v, x2, x4, at, 1.0, m);
 #pragma unroll
   for (int k = 0; k < 4; k++) b[k] = -m[k];
-  solve_moment(U, V, lam, b, A);
+  solve_moment(ms, b, A);
   // half-space moments of this side
   moments_half<7>(U, lam, h, sgn, u);
   double t[4];
@@ -246,22 +281,23 @@ __global__ void __launch_bounds__(128) k_flux(Dev d) {
   double up[7], un[7], uf[7], v0[6];
   moments_full<7>(U0, h0, uf);
   moments_full<6>(V0, h0, v0);
-  moments_half<7>(U0, lam0, h0, 1.0, up);
-  moments_half<7>(U0, lam0, h0, -1.0, un);
+  moments_half_pair<7>(U0, lam0, h0, up, un);
+  const MSolve ms0 = msolve(U0, V0, lam0, h0);
   const double x2 = KDOF * h0, x4 = KDOF * (KDOF + 2) * h0 * h0;
   double abl[4], abr[4], abt[4], Ab[4];
   {
     double b[4];
     const double ir0 = 1.0 / r0;
+    const double sl = ir0 / dL, sr = ir0 / dR;
 #pragma unroll
-    for (int k = 0; k < 4; k++) b[k] = (acc.W0[k] - WcL[k]) / dL * ir0;
-    solve_moment(U0, V0, lam0, b, abl);
+    for (int k = 0; k < 4; k++) b[k] = (acc.W0[k] - WcL[k]) * sl;
+    solve_moment(ms0, b, abl);
 #pragma unroll
-    for (int k = 0; k < 4; k++) b[k] = (WcR[k] - acc.W0[k]) / dR * ir0;
-    solve_moment(U0, V0, lam0, b, abr);
+    for (int k = 0; k < 4; k++) b[k] = (WcR[k] - acc.W0[k]) * sr;
+    solve_moment(ms0, b, abr);
 #pragma unroll
     for (int k = 0; k < 4; k++) b[k] = 0.5 * (SLt[k] + SRt[k]) * ir0;
-    solve_moment(U0, V0, lam0, b, abt);
+    solve_moment(ms0, b, abt);
   }
   // Eq. 12 (reduced): <(abar_l u H + abar_r u (1-H) + abar_t v + Abar) psi>_g0 = 0
   double sq1[4] = {0, 0, 0, 0};
@@ -272,7 +308,7 @@ __global__ void __launch_bounds__(128) k_flux(Dev d) {
     double b[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) b[k] = -sq1[k];
-    solve_moment(U0, V0, lam0, b, Ab);
+    solve_moment(ms0, b, Ab);
   }
 
   // ---- collision time (Eq. 33-34 + pressure-jump term) and time weights ----
@@ -306,7 +342,7 @@ __global__ void __launch_bounds__(128) k_flux(Dev d) {
   const double e0 = U0 * U0 + V0 * V0;
   const double heat = Fn[3] - U0 * Fn[1] - V0 * Fn[2] + 0.5 * e0 * Fn[0] - U0 * Ws[3] + U0 * U0 * Fn[0]
                     + U0 * V0 * Ws[2] - 0.5 * U0 * e0 * Ws[0];
-  Fn[3] += (1.0 / fl.prandtl - 1.0) * heat;
+  Fn[3] += fl.pr_fix * heat;
 
   // ---- back to the global frame, times the face length ----
   d.F[f] = Fn[0] * S;
@@ -317,11 +353,12 @@ __global__ void __launch_bounds__(128) k_flux(Dev d) {
   // ---- SA face terms (Eq. 28-30) and the coefficients of its implicit system ----
   double o4 = 0.0, o5 = 0.0, aLR = 0.0, aRL = 0.0, dgl = 0.0, dgr = 0.0;
   if (fl.sa_on) {
-    const double dn = d.fdn[f];
-    const double vni = (WcLg[1] * nx + WcLg[2] * ny) / WcLg[0];
-    const double vnj = (WcRg[1] * nx + WcRg[2] * ny) / WcRg[0];
-    const double nui = d.mu_l[L] / WcLg[0], nuj = muR / WcRg[0];
-    const double gradn = (WcRg[4] - WcLg[4]) / dn;
+    const double idn = 1.0 / d.fdn[f];
+    const double irl = 1.0 / WcLg[0], irr = 1.0 / WcRg[0];
+    const double vni = (WcLg[1] * nx + WcLg[2] * ny) * irl;
+    const double vnj = (WcRg[1] * nx + WcRg[2] * ny) * irr;
+    const double nui = d.mu_l[L] * irl, nuj = muR * irr;
+    const double gradn = (WcRg[4] - WcLg[4]) * idn;
     const double finv = fmax(vni, 0.0) * WcLg[4] + fmin(vnj, 0.0) * WcRg[4];
     const double kap = 1.0 / (2.0 * SA_SIGMA) * ((nui + nuj) + (1.0 + SA_CB2) * (WcLg[4] + WcRg[4]));
     const double fvis = kap * gradn;
@@ -329,7 +366,7 @@ __global__ void __launch_bounds__(128) k_flux(Dev d) {
     const double fadr = SA_CB2 / SA_SIGMA * WcRg[4] * (-gradn);
     o4 = (-finv + fvis - fadl) * S;
     o5 = (finv - fvis - fadr) * S;
-    const double kd = kap / dn;
+    const double kd = kap * idn;
     aLR = S * (fmin(vnj, 0.0) - kd);
     aRL = S * (fmin(-vni, 0.0) - kd);
     dgl = S * (fmax(vni, 0.0) + kd);
