@@ -75,7 +75,10 @@ typedef struct igks_options {
   int32_t timing;         /* record CUDA events around every kernel (igks_kernel_times) */
   int32_t sweep_mode;     /* 0 automatic, 1 one block per solve walking its levels,
                              2 one launch per level over all solves (low-depth orderings) */
-  int32_t reserved[5];
+  int32_t sweep_cluster;  /* schedule 1: a thread-block cluster of 1 (0: 1), 2, 4 or 8 blocks per
+                             solve shares each level (distributed shared memory, one cluster
+                             barrier per level); same arithmetic, same bits */
+  int32_t reserved[4];
 } igks_options;
 
 /* Flow conditions of one solve. Non-dimensional: free-stream density, speed and the
@@ -209,6 +212,7 @@ typedef struct igks_tuning {
   int32_t sweep_threads;   /* threads per block of the one-block-per-solve sweeps */
   int32_t flux_block;      /* threads per block of the flux kernel */
   int32_t sweep_mode;      /* 1 one block per solve, 2 one launch per level */
+  int32_t sweep_cluster;   /* blocks per solve of schedule 1 */
   float ms_per_iter;       /* measured device time of one iteration with it */
 } igks_tuning;
 

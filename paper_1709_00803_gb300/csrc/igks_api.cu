@@ -428,6 +428,7 @@ static int build(igks_ctx* ctx) {
     }
     int mode = ctx->opt.sweep_mode;
     d.wide = (mode == 2) || (mode == 0 && std::max(maxf, maxb) <= WIDE_MAX_LEVELS);
+    d.sweep_cluster = ctx->opt.sweep_cluster;
     std::vector<int> wf, wb;
     ctx->h_wfwd_ptr.assign(1, 0);
     ctx->h_wbwd_ptr.assign(1, 0);
@@ -509,6 +510,9 @@ int igks_create(const igks_options* opt, igks_ctx** out) {
   if (ctx->opt.sweep_threads <= 0) ctx->opt.sweep_threads = NARROW_THREADS;
   if (ctx->opt.sweep_threads > NARROW_THREADS || ctx->opt.sweep_threads % 32) { delete ctx; return IGKS_EINVAL; }
   if (ctx->opt.precision != IGKS_PREC_FP64 && ctx->opt.precision != IGKS_PREC_MIXED) { delete ctx; return IGKS_EINVAL; }
+  if (ctx->opt.sweep_cluster <= 0) ctx->opt.sweep_cluster = 1;
+  if (ctx->opt.sweep_cluster != 1 && ctx->opt.sweep_cluster != 2 && ctx->opt.sweep_cluster != 4 &&
+      ctx->opt.sweep_cluster != 8) { delete ctx; return IGKS_EINVAL; }
   cudaError_t e = cudaSetDevice(ctx->opt.device);
   if (e != cudaSuccess) { delete ctx; return IGKS_ECUDA; }
   if (ctx->opt.stream) {
@@ -957,13 +961,16 @@ int igks_autotune(igks_ctx* ctx, int32_t iters_per_trial, igks_tuning* out) {
   const bool wide_ok = std::max(d.n_wfwd, d.n_wbwd) <= 4 * WIDE_MAX_LEVELS;
   const int flux_blocks[] = {64, 128};
   const int sweep_threads[] = {128, 256};
+  const int clusters[] = {1, 2, 4};
   int err = 0;
   for (int wide = 0; wide <= (wide_ok ? 1 : 0) && !err; wide++)
     for (int fb : flux_blocks)
-      for (int stt : sweep_threads) {
-        if (wide && stt != sweep_threads[0]) continue;   // the wide schedule has its own block
+      for (int stt : sweep_threads)
+        for (int cl : clusters) {
+        if (wide && (stt != sweep_threads[0] || cl != 1)) continue;   // the wide schedule has its own block
         d.wide = wide;
         d.flux_block = fb;
+        d.sweep_cluster = cl;
         ctx->opt.sweep_threads = stt;
         if ((err = recapture(ctx))) break;
         restore();
@@ -977,13 +984,15 @@ int igks_autotune(igks_ctx* ctx, int32_t iters_per_trial, igks_tuning* out) {
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
         ms /= iters_per_trial;
-        if (ms < best.ms_per_iter) best = igks_tuning{stt, fb, wide ? 2 : 1, ms};
-      }
+        if (ms < best.ms_per_iter) best = igks_tuning{stt, fb, wide ? 2 : 1, cl, ms};
+        }
   // apply the winner and put every solve back where it was
   d.wide = best.sweep_mode == 2;
   d.flux_block = best.flux_block;
+  d.sweep_cluster = best.sweep_cluster;
   ctx->opt.sweep_threads = best.sweep_threads;
   ctx->opt.sweep_mode = best.sweep_mode;
+  ctx->opt.sweep_cluster = best.sweep_cluster;
   if (!err) err = recapture(ctx);
   restore();
   cudaStreamSynchronize(ctx->stream);

@@ -112,6 +112,7 @@ struct Dev {
   const int* cf_to_ef; const int* cf_to_eb;      // [nnz] e * P + p, or -1
   // wide schedule: cells of each level of all solves
   int wide;                      // 1: one launch per level; 0: one block per solve
+  int sweep_cluster;             // narrow schedule: blocks (a thread-block cluster) per solve
   const int* wfwd_cells; const int* wbwd_cells;
   const int* h_wfwd_ptr; const int* h_wbwd_ptr;   // HOST arrays of level offsets (launch sizes)
   int n_wfwd, n_wbwd;

@@ -18,10 +18,13 @@
 //    stored in sweep-position order so it is fetched without an indirection;
 //  - wide: one launch per level covering that level's cells of every solve (for low-depth
 //    orderings, e.g. multicolour, whose few levels hold thousands of cells each).
+#include <cooperative_groups.h>
 #include <float.h>
 
 #include "igks_dev.h"
 #include "igks_phys.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace igks {
 
@@ -173,7 +176,7 @@ __device__ __forceinline__ void fwd_cell(const Dev& d, int i, bool sa_on) {
 
 __device__ __forceinline__ void flush_eq40(const Dev& d, int s, double eq40, int bad);
 
-template <class T>
+template <class T, int C>
 __device__ __forceinline__ void bwd_entry(const Dev& d, const T* ring, const T* dF, const T* dWo, int j, int slot,
                                           const T* ws, T sx, T sy, T sl, T sa, bool sa_on, T* acc);
 
@@ -199,7 +202,7 @@ __device__ __forceinline__ void bwd_cell(const Dev& d, int i, bool sa_on) {
       if (d.fbc[f] == 1 || d.fbc[f] == 4) continue;  // free-stream and outflow increments are zero
       j = -1 - f;
     }
-    bwd_entry<T>(d, nullptr, dF, dWo, j, -1, ws, sc[k], sc[nnz + k], sc[2 * nnz + k], sc[3 * nnz + k], sa_on, acc);
+    bwd_entry<T, 1>(d, nullptr, dF, dWo, j, -1, ws, sc[k], sc[nnz + k], sc[2 * nnz + k], sc[3 * nnz + k], sa_on, acc);
   }
   T dw[5];
 #pragma unroll
@@ -290,15 +293,30 @@ __device__ __forceinline__ void ring_put(T* ring, int slot, const T* o, const T*
   for (int v = 0; v < 5; v++) ring[(8 + v) * RING + slot] = dw[v];
 }
 
-template <class T>
+// With a cluster of C blocks per solve (C > 1), position q of the solve belongs to block
+// q % C and its increments sit in that block's ring, read through distributed shared
+// memory; RING is a multiple of C, so the slot q % RING names the owner too.
+template <class T, int C>
+__device__ __forceinline__ const T* ring_of(const T* ring, int slot) {
+  if constexpr (C == 1) {
+    return ring;
+  } else {
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned owner = (unsigned)(slot & (C - 1));
+    return owner == cl.block_rank() ? ring : cl.map_shared_rank(ring, owner);
+  }
+}
+
+template <class T, int C = 1>
 __device__ __forceinline__ void neighbour(const Dev& d, const T* ring, const T* dF, const T* dWv, int j, int slot,
                                           T* f, T* w) {
   const int n = d.nc_pad;
   if (slot >= 0) {
+    const T* rb = ring_of<T, C>(ring, slot);
 #pragma unroll
-    for (int k = 0; k < 8; k++) f[k] = ring[k * RING + slot];
+    for (int k = 0; k < 8; k++) f[k] = rb[k * RING + slot];
 #pragma unroll
-    for (int v = 0; v < 5; v++) w[v] = ring[(8 + v) * RING + slot];
+    for (int v = 0; v < 5; v++) w[v] = rb[(8 + v) * RING + slot];
   } else {
 #pragma unroll
     for (int k = 0; k < 8; k++) f[k] = dF[k * n + j];
@@ -380,7 +398,7 @@ __device__ __forceinline__ void fwd_load_direct(const Dev& d, int p, FwdRec<T>* 
   }
 }
 
-template <class T>
+template <class T, int C = 1>
 __device__ __forceinline__ void fwd_process(const Dev& d, T* ring, int p, int pbase, const FwdRec<T>* r, bool sa_on) {
   const int n = d.nc_pad, P = d.npos;
   T* dWs = (T*)d.dWs;
@@ -394,7 +412,7 @@ __device__ __forceinline__ void fwd_process(const Dev& d, T* ring, int p, int pb
     for (int e = 0; e < PF_E; e++) {
       if (e >= cnt) break;
       T f[8], w[5];
-      neighbour<T>(d, ring, dF, dWs, r->j[e], r->slot[e], f, w);
+      neighbour<T, C>(d, ring, dF, dWs, r->j[e], r->slot[e], f, w);
       fwd_acc<T>(acc, r->co[0][e], r->co[1][e], r->co[2][e], r->co[3][e], f, w, sa_on);
     }
   } else {
@@ -403,7 +421,7 @@ __device__ __forceinline__ void fwd_process(const Dev& d, T* ring, int p, int pb
     const int nfs = d.nfs;
     for (int k = d.fs_ptr[p]; k < d.fs_ptr[p + 1]; k++) {
       T f[8], w[5];
-      neighbour<T>(d, ring, dF, dWs, d.fs_j[k], d.fs_slot[k], f, w);
+      neighbour<T, C>(d, ring, dF, dWs, d.fs_j[k], d.fs_slot[k], f, w);
       fwd_acc<T>(acc, sc[k], sc[nfs + k], sc[2 * nfs + k], sc[3 * nfs + k], f, w, sa_on);
     }
   }
@@ -426,39 +444,58 @@ __device__ __forceinline__ void fwd_process(const Dev& d, T* ring, int p, int pb
   for (int k = 0; k < 8; k++) dF[k * n + i] = o[k];
 }
 
-template <class T>
+// the first position at or after b that belongs to cluster block r (positions q = p - pbase
+// are dealt round the C blocks: q % C == r)
+template <int C>
+__device__ __forceinline__ int first_own(int b, int pbase, int r) {
+  if constexpr (C == 1) return b;
+  return b + (((r - (b - pbase)) % C) + C) % C;
+}
+
+template <int C>
+__device__ __forceinline__ void level_barrier() {
+  if constexpr (C == 1) __syncthreads();
+  else cg::this_cluster().sync();   // release/acquire over the cluster's shared and global writes
+}
+
+template <class T, int C>
 __global__ void __launch_bounds__(NARROW_THREADS) k_sweep_fwd_narrow(Dev d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = (T*)smem_raw;
   FwdRec<T>* stage = (FwdRec<T>*)(smem_raw + (size_t)13 * RING * sizeof(T));
   FwdRec<T>* st = stage + threadIdx.x;               // staged record of this thread's next position
-  const int s = blockIdx.x;
-  if (d.st[s].state != 0 || d.flow[s].scheme == 1) return;
+  const int s = blockIdx.x / C, r = blockIdx.x % C;  // one cluster of C blocks per solve
+  if (d.st[s].state != 0 || d.flow[s].scheme == 1) return;   // uniform over the cluster
+  if constexpr (C > 1) cg::this_cluster().sync();    // every block runs before any remote read
   const bool sa_on = d.flow[s].sa_on;
   const int l0 = d.lvl_solve_ptr[s], l1 = d.lvl_solve_ptr[s + 1] - 1;
   const int pbase = d.fwd_lvl[l0];
+  const int step = C * (int)blockDim.x;
   // level bounds travel in registers: level l spans [b, e), the next one [e, en)
   int b = d.fwd_lvl[l0], e = d.fwd_lvl[l0 + 1];
-  if (l0 < l1 && b + (int)threadIdx.x < e) fwd_stage<T>(d, b + threadIdx.x, st);
+  int pm = first_own<C>(b, pbase, r) + C * (int)threadIdx.x;    // this thread's position of the level
+  if (l0 < l1 && pm < e) fwd_stage<T>(d, pm, st);
   for (int l = l0; l < l1; l++) {
     const int en = (l + 1 < l1) ? d.fwd_lvl[l + 2] : e;
-    const bool mine = b + (int)threadIdx.x < e;
+    const bool mine = pm < e;
     FwdRec<T> cur;
     if (mine) {
       cpa_wait_all();
       cur = *st;                 // this level's record into registers, freeing the stage
     }
     // the next level's record is in flight while this level is computed
-    if (e + (int)threadIdx.x < en) fwd_stage<T>(d, e + threadIdx.x, st);
-    if (mine) fwd_process<T>(d, ring, b + threadIdx.x, pbase, &cur, sa_on);
-    for (int p = b + threadIdx.x + blockDim.x; p < e; p += blockDim.x) {   // levels wider than the block
+    const int pn = first_own<C>(e, pbase, r) + C * (int)threadIdx.x;
+    if (pn < en) fwd_stage<T>(d, pn, st);
+    if (mine) fwd_process<T, C>(d, ring, pm, pbase, &cur, sa_on);
+    for (int p = pm + step; p < e; p += step) {   // levels wider than the cluster's threads
       FwdRec<T> xt;
       fwd_load_direct<T>(d, p, &xt);
-      fwd_process<T>(d, ring, p, pbase, &xt, sa_on);
+      fwd_process<T, C>(d, ring, p, pbase, &xt, sa_on);
     }
-    __syncthreads();
+    level_barrier<C>();
     b = e;
     e = en;
+    pm = pn;
   }
 }
 
@@ -520,12 +557,12 @@ __device__ __forceinline__ void bwd_load_direct(const Dev& d, int p, BwdRec<T>* 
 // contribution of one backward entry: upper neighbour j (its increments from the ring or
 // global memory), or a wall/symmetry ghost (j = -1 - face: boundary map of this cell's
 // own forward increment ws, flux increment about the ghost state)
-template <class T>
+template <class T, int C>
 __device__ __forceinline__ void bwd_entry(const Dev& d, const T* ring, const T* dF, const T* dWo, int j, int slot,
                                           const T* ws, T sx, T sy, T sl, T sa, bool sa_on, T* acc) {
   T f[8], w[5];
   if (j >= 0) {
-    neighbour<T>(d, ring, dF, dWo, j, slot, f, w);
+    neighbour<T, C>(d, ring, dF, dWo, j, slot, f, w);
   } else {
     const int nf = d.nf, fc = -1 - j;
     w[0] = ws[0]; w[3] = ws[3];
@@ -543,7 +580,7 @@ __device__ __forceinline__ void bwd_entry(const Dev& d, const T* ring, const T* 
   bwd_acc<T>(acc, sx, sy, sl, sa, f, w, sa_on);
 }
 
-template <class T>
+template <class T, int C = 1>
 __device__ __forceinline__ void bwd_process(const Dev& d, T* ring, int p, int pbase, const BwdRec<T>* r, bool sa_on) {
   const int n = d.nc_pad;
   T* dWo = (T*)d.dW;
@@ -557,15 +594,15 @@ __device__ __forceinline__ void bwd_process(const Dev& d, T* ring, int p, int pb
 #pragma unroll
     for (int e = 0; e < PF_E; e++) {
       if (e >= cnt) break;
-      bwd_entry<T>(d, ring, dF, dWo, r->j[e], r->slot[e], ws, r->co[0][e], r->co[1][e], r->co[2][e], r->co[3][e],
-                   sa_on, acc);
+      bwd_entry<T, C>(d, ring, dF, dWo, r->j[e], r->slot[e], ws, r->co[0][e], r->co[1][e], r->co[2][e],
+                      r->co[3][e], sa_on, acc);
     }
   } else {
     const T* sc = (const T*)d.sc_b;
     const int nbs = d.nbs;
     for (int k = d.bs_ptr[p]; k < d.bs_ptr[p + 1]; k++)
-      bwd_entry<T>(d, ring, dF, dWo, d.bs_j[k], d.bs_slot[k], ws, sc[k], sc[nbs + k], sc[2 * nbs + k],
-                   sc[3 * nbs + k], sa_on, acc);
+      bwd_entry<T, C>(d, ring, dF, dWo, d.bs_j[k], d.bs_slot[k], ws, sc[k], sc[nbs + k], sc[2 * nbs + k],
+                      sc[3 * nbs + k], sa_on, acc);
   }
   T dw[5];
 #pragma unroll
@@ -581,37 +618,42 @@ __device__ __forceinline__ void bwd_process(const Dev& d, T* ring, int p, int pb
   for (int k = 0; k < 8; k++) dF[k * n + i] = o[k];
 }
 
-template <class T>
+template <class T, int C>
 __global__ void __launch_bounds__(NARROW_THREADS) k_sweep_bwd_narrow(Dev d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = (T*)smem_raw;
   BwdRec<T>* stage = (BwdRec<T>*)(smem_raw + (size_t)13 * RING * sizeof(T));
   BwdRec<T>* st = stage + threadIdx.x;
-  const int s = blockIdx.x;
+  const int s = blockIdx.x / C, r = blockIdx.x % C;
   if (d.st[s].state != 0 || d.flow[s].scheme == 1) return;
+  if constexpr (C > 1) cg::this_cluster().sync();
   const bool sa_on = d.flow[s].sa_on;
   const int l0 = d.blvl_solve_ptr[s], l1 = d.blvl_solve_ptr[s + 1] - 1;
   const int pbase = d.bwd_lvl[l0];
+  const int step = C * (int)blockDim.x;
   int b = d.bwd_lvl[l0], e = d.bwd_lvl[l0 + 1];
-  if (l0 < l1 && b + (int)threadIdx.x < e) bwd_stage<T>(d, b + threadIdx.x, st);
+  int pm = first_own<C>(b, pbase, r) + C * (int)threadIdx.x;
+  if (l0 < l1 && pm < e) bwd_stage<T>(d, pm, st);
   for (int l = l0; l < l1; l++) {
     const int en = (l + 1 < l1) ? d.bwd_lvl[l + 2] : e;
-    const bool mine = b + (int)threadIdx.x < e;
+    const bool mine = pm < e;
     BwdRec<T> cur;
     if (mine) {
       cpa_wait_all();
       cur = *st;
     }
-    if (e + (int)threadIdx.x < en) bwd_stage<T>(d, e + threadIdx.x, st);
-    if (mine) bwd_process<T>(d, ring, b + threadIdx.x, pbase, &cur, sa_on);
-    for (int p = b + threadIdx.x + blockDim.x; p < e; p += blockDim.x) {   // levels wider than the block
+    const int pn = first_own<C>(e, pbase, r) + C * (int)threadIdx.x;
+    if (pn < en) bwd_stage<T>(d, pn, st);
+    if (mine) bwd_process<T, C>(d, ring, pm, pbase, &cur, sa_on);
+    for (int p = pm + step; p < e; p += step) {
       BwdRec<T> xt;
       bwd_load_direct<T>(d, p, &xt);
-      bwd_process<T>(d, ring, p, pbase, &xt, sa_on);
+      bwd_process<T, C>(d, ring, p, pbase, &xt, sa_on);
     }
-    __syncthreads();
+    level_barrier<C>();
     b = e;
     e = en;
+    pm = pn;
   }
 }
 
@@ -650,11 +692,49 @@ static size_t fwd_smem() { return (size_t)13 * RING * sizeof(T) + (size_t)NARROW
 template <class T>
 static size_t bwd_smem() { return (size_t)13 * RING * sizeof(T) + (size_t)NARROW_THREADS * sizeof(BwdRec<T>); }
 
+template <class T, int C>
+static void set_smem() {
+  cudaFuncSetAttribute(k_sweep_fwd_narrow<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<T>());
+  cudaFuncSetAttribute(k_sweep_bwd_narrow<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<T>());
+}
+
 void setup_sweeps() {
-  cudaFuncSetAttribute(k_sweep_fwd_narrow<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<double>());
-  cudaFuncSetAttribute(k_sweep_bwd_narrow<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<double>());
-  cudaFuncSetAttribute(k_sweep_fwd_narrow<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<float>());
-  cudaFuncSetAttribute(k_sweep_bwd_narrow<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<float>());
+  set_smem<double, 1>(); set_smem<double, 2>(); set_smem<double, 4>(); set_smem<double, 8>();
+  set_smem<float, 1>(); set_smem<float, 2>(); set_smem<float, 4>(); set_smem<float, 8>();
+}
+
+// one block per solve (C = 1), or one cluster of C blocks per solve
+template <class T, int C>
+static void launch_narrow(bool fwd, const Dev& d, int threads, cudaStream_t s) {
+  void (*k)(Dev) = fwd ? k_sweep_fwd_narrow<T, C> : k_sweep_bwd_narrow<T, C>;
+  const size_t smem = fwd ? fwd_smem<T>() : bwd_smem<T>();
+  if (C == 1) {
+    k<<<d.n_solves, threads, smem, s>>>(d);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(d.n_solves * C));
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, d);
+}
+
+template <class T>
+static void launch_narrow_c(bool fwd, const Dev& d, int threads, cudaStream_t s) {
+  switch (d.sweep_cluster) {
+    case 2: launch_narrow<T, 2>(fwd, d, threads, s); break;
+    case 4: launch_narrow<T, 4>(fwd, d, threads, s); break;
+    case 8: launch_narrow<T, 8>(fwd, d, threads, s); break;
+    default: launch_narrow<T, 1>(fwd, d, threads, s); break;
+  }
 }
 
 void launch_sweep_prep(const Dev& d, int precision, cudaStream_t s) {
@@ -672,8 +752,8 @@ void launch_sweep_fwd(const Dev& d, int precision, int threads, cudaStream_t s) 
     }
     return;
   }
-  if (precision == 1) k_sweep_fwd_narrow<float><<<d.n_solves, threads, fwd_smem<float>(), s>>>(d);
-  else k_sweep_fwd_narrow<double><<<d.n_solves, threads, fwd_smem<double>(), s>>>(d);
+  if (precision == 1) launch_narrow_c<float>(true, d, threads, s);
+  else launch_narrow_c<double>(true, d, threads, s);
 }
 
 void launch_sweep_bwd(const Dev& d, int precision, int threads, cudaStream_t s) {
@@ -686,8 +766,8 @@ void launch_sweep_bwd(const Dev& d, int precision, int threads, cudaStream_t s) 
     }
     return;
   }
-  if (precision == 1) k_sweep_bwd_narrow<float><<<d.n_solves, threads, bwd_smem<float>(), s>>>(d);
-  else k_sweep_bwd_narrow<double><<<d.n_solves, threads, bwd_smem<double>(), s>>>(d);
+  if (precision == 1) launch_narrow_c<float>(false, d, threads, s);
+  else launch_narrow_c<double>(false, d, threads, s);
 }
 
 }  // namespace igks

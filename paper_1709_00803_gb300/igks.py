@@ -27,7 +27,8 @@ class IgksError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
                 ("check_every", C.c_int32), ("use_graph", C.c_int32), ("sweep_threads", C.c_int32),
-                ("timing", C.c_int32), ("sweep_mode", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("timing", C.c_int32), ("sweep_mode", C.c_int32), ("sweep_cluster", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
 
 class Flow(C.Structure):
@@ -42,7 +43,7 @@ class Flow(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("sweep_threads", C.c_int32), ("flux_block", C.c_int32), ("sweep_mode", C.c_int32),
-                ("ms_per_iter", C.c_float)]
+                ("sweep_cluster", C.c_int32), ("ms_per_iter", C.c_float)]
 
 
 class Status(C.Structure):
@@ -205,9 +206,10 @@ class Context:
     """One igks_ctx: a set of steady solves resident on one GPU."""
 
     def __init__(self, precision=PREC_FP64, device=0, stream=None, check_every=20, use_graph=1,
-                 sweep_threads=0, timing=0, sweep_mode=0):
+                 sweep_threads=0, timing=0, sweep_mode=0, sweep_cluster=0):
         o = Options(precision=precision, device=device, stream=stream, check_every=check_every,
-                    use_graph=use_graph, sweep_threads=sweep_threads, timing=timing, sweep_mode=sweep_mode)
+                    use_graph=use_graph, sweep_threads=sweep_threads, timing=timing, sweep_mode=sweep_mode,
+                    sweep_cluster=sweep_cluster)
         h = C.c_void_p()
         rc = lib().igks_create(C.byref(o), C.byref(h))
         if rc:

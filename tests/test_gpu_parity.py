@@ -257,3 +257,30 @@ def test_explicit_scheme_matches_oracle(mk, flow_fn):
         _compare_iteration(ctx, sid, ora, skip=("dwstar", "dw"))
         ctx.iterate(6); ora.iterate(6)
         assert_close("W after 7 explicit steps", ctx.get_fields(sid), ora.get(O.ORA_W), TOL)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cluster_sweeps_bitwise_equal_one_block(precision):
+    """A cluster of C blocks per solve shares every level of the sweeps (distributed shared
+    memory, one cluster barrier per level) and does the same arithmetic in the same order:
+    the iterates are bitwise those of one block per solve, alone and in a batch."""
+    from paper_1709_00803_gb300 import igks
+    cases = [(G.flat_plate_hybrid(nx=48, nq=16, ntri_rows=12, first=1e-5, seed=3), F.turbulent_plate_flow(), 1),
+             (G.mixed_polygons(), F.turbulent_plate_flow(), 2),
+             (G.laminar_plate(), F.laminar_plate_flow(), 3)]
+    ref = None
+    for cl in (1, 2, 4, 8):
+        ctx = igks.Context(precision=precision, sweep_mode=1, sweep_cluster=cl)
+        for m, fl, seed in cases:
+            sid = ctx.mesh_upload(m); ctx.set_flow(sid, fl)
+        for k, (m, fl, seed) in enumerate(cases):
+            ctx.init_freestream(k)
+            ctx.set_fields(k, seeded(m, fl, seed))
+        ctx.iterate(6)
+        out = [ctx.get_fields(k) for k in range(len(cases))]
+        ctx.destroy()
+        if ref is None:
+            ref = out
+        else:
+            for k in range(len(cases)):
+                assert np.array_equal(out[k], ref[k]), f"cluster {cl}, solve {k}"
