@@ -59,7 +59,8 @@ def alg_bytes(kernel, t, nc, nf):
     once, neighbour re-reads from cache. t = bytes of the sweep type."""
     cell_flux_inputs = 21 * 8          # W 5, gradient 8, limiter 4, centroid 2, mu 2
     per = {
-        "k_gradient": nc * (5 * 8 + 2 * 8 + 2 * 8 + 8 * 8 + 4 * 8 + 8 + 8 + 8) + nf * (2 * 4 + 5 * 8 + 8),
+        "k_ghost": nc * (5 * 8 + 2 * 8) + nf * (3 * 4 + 3 * 8 + 8),   # states, viscosities, face ids/geometry, lambda_f
+        "k_gradient": nc * (5 * 8 + 2 * 8 + 8 + 8 * 8 + 4 * 8 + 8 + 8) + nf * (2 * 4 + 8 + 8),
         "k_flux": nf * (4 * 4 + 8 * 8 + 10 * 8) + nc * cell_flux_inputs,
         "k_residual": nc * (8 + 8 * 8 + 5 * 8 + 3 * 8) + nf * (6 * 8 + 4 * 8),
         "k_sweep_fwd": nc * (13 * t + 3 * 4 + 4 * (2 * 4 + 4 * t) + 18 * t),

@@ -126,41 +126,13 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_prep(Dev d) {
   d.mu_t[i] = eddy_viscosity(fl, r, nut, mu);
 }
 
-// ghost states of the boundary faces
-__global__ void k_ghost(Dev d) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= d.nbf) return;
-  int f = d.bface[k];
-  int s = d.fsolve[f];
-  if (d.st[s].state != 0) return;
-  const DevFlow& fl = d.flow[s];
-  int i = d.fL[f], n = d.nc_pad;
-  double Wi[5], Wg[5];
-  for (int v = 0; v < 5; v++) Wi[v] = d.W[v * n + i];
-  ghost_state(fl, d.fbc[f], d.fnx[f], d.fny[f], Wi, Wg);
-  for (int v = 0; v < 5; v++) d.G[v * d.nf + f] = Wg[v];
-  double mu = viscosity(fl, lambda_of(Wg[0], Wg[1], Wg[2], Wg[3]));
-  d.Gmu[f] = mu;
-  d.Gmu[d.nf + f] = eddy_viscosity(fl, Wg[0], Wg[4], mu);
-}
-
-void launch_prep(const Dev& d, cudaStream_t s) {
-  k_prep<<<d.n_cell_blocks, CELL_BLOCK, 0, s>>>(d);
-}
-
-void launch_ghost(const Dev& d, cudaStream_t s) {
-  if (d.nbf) k_ghost<<<(d.nbf + 127) / 128, 128, 0, s>>>(d);
-}
-
-// state and viscosities of the cell across face f (ghost on a boundary)
-__device__ __forceinline__ void across_state(const Dev& d, int f, int j, double* Wk, double* mu, double* mut) {
+// state of the cell across face f (ghost on a boundary)
+__device__ __forceinline__ void across_W(const Dev& d, int f, int j, double* Wk) {
   if (j >= 0) {
     int n = d.nc_pad;
     for (int v = 0; v < 5; v++) Wk[v] = d.W[v * n + j];
-    *mu = d.mu_l[j]; *mut = d.mu_t[j];
   } else {
     for (int v = 0; v < 5; v++) Wk[v] = d.G[v * d.nf + f];
-    *mu = d.Gmu[f]; *mut = d.Gmu[d.nf + f];
   }
 }
 
@@ -182,9 +154,43 @@ __device__ __forceinline__ double face_lambda(const DevFlow& fl, const double* W
   return lam;
 }
 
+// per face: the ghost state of a boundary face (Section II.E) and the face spectral
+// radius lambda_f of Eq. 21 (computed once per face, read by both cells' Lambda sums)
+__global__ void k_ghost(Dev d) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= d.nf) return;
+  int s = d.fsolve[f];
+  if (d.st[s].state != 0) return;
+  const DevFlow& fl = d.flow[s];
+  const int L = d.fL[f], R = d.fR[f], n = d.nc_pad;
+  double WL[5], WR[5], muR, mtR;
+  for (int v = 0; v < 5; v++) WL[v] = d.W[v * n + L];
+  if (R < 0) {
+    ghost_state(fl, d.fbc[f], d.fnx[f], d.fny[f], WL, WR);
+    for (int v = 0; v < 5; v++) d.G[v * d.nf + f] = WR[v];
+    muR = viscosity(fl, lambda_of(WR[0], WR[1], WR[2], WR[3]));
+    mtR = eddy_viscosity(fl, WR[0], WR[4], muR);
+    d.Gmu[f] = muR;
+    d.Gmu[d.nf + f] = mtR;
+  } else {
+    for (int v = 0; v < 5; v++) WR[v] = d.W[v * n + R];
+    muR = d.mu_l[R];
+    mtR = d.mu_t[R];
+  }
+  d.lam_f[f] = face_lambda(fl, WL, WR, d.mu_l[L], d.mu_t[L], muR, mtR, d.fnx[f], d.fny[f], d.fdn[f]);
+}
+
+void launch_prep(const Dev& d, cudaStream_t s) {
+  k_prep<<<d.n_cell_blocks, CELL_BLOCK, 0, s>>>(d);
+}
+
+void launch_ghost(const Dev& d, cudaStream_t s) {
+  if (d.nf) k_ghost<<<(d.nf + 127) / 128, 128, 0, s>>>(d);
+}
+
 // Least-squares gradients (Eq. 7) of the conserved variables over the face neighbours
-// (ghosts included), the limiter of Eq. 9-10, the vorticity for SA, the face spectral
-// radius, Lambda_i and the per-solve minimum explicit time step (Eq. 23).
+// (ghosts included), the limiter of Eq. 9-10, the vorticity for SA, Lambda_i from the face
+// spectral radii and the per-solve minimum explicit time step (Eq. 23).
 __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x, s = -1;
   bool live = cell_live(d, i, &s);
@@ -194,7 +200,6 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
     const int n = d.nc_pad;
     double Wi[5];
     for (int v = 0; v < 5; v++) Wi[v] = d.W[v * n + i];
-    double mui = d.mu_l[i], mti = d.mu_t[i];
     double xi = d.cx[i], yi = d.cy[i];
     double A00 = 0.0, A01 = 0.0, A11 = 0.0;
     double r0[4] = {0, 0, 0, 0}, r1[4] = {0, 0, 0, 0}, wmax[4], wmin[4];
@@ -203,10 +208,9 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
     for (int k = d.cf_ptr[i]; k < d.cf_ptr[i + 1]; k++) {
       int f = d.cf_face[k];
       int L = d.fL[f], R = d.fR[f];
-      bool own = (L == i);
-      int j = own ? R : L;
-      double Wk[5], muk, mtk, xk, yk;
-      across_state(d, f, j, Wk, &muk, &mtk);
+      int j = (L == i) ? R : L;
+      double Wk[5], xk, yk;
+      across_W(d, f, j, Wk);
       if (j >= 0) { xk = d.cx[j]; yk = d.cy[j]; } else { xk = d.fcx[f]; yk = d.fcy[f]; }
       double dx = xk - xi, dy = yk - yi;
       A00 += dx * dx; A01 += dx * dy; A11 += dy * dy;
@@ -218,10 +222,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
         wmax[v] = fmax(wmax[v], Wk[v]);
         wmin[v] = fmin(wmin[v], Wk[v]);
       }
-      double lam = own ? face_lambda(fl, Wi, Wk, mui, mti, muk, mtk, d.fnx[f], d.fny[f], d.fdn[f])
-                       : face_lambda(fl, Wk, Wi, muk, mtk, mui, mti, d.fnx[f], d.fny[f], d.fdn[f]);
-      if (own) d.lam_f[f] = lam;
-      Lam += 0.5 * lam * d.fS[f];
+      Lam += 0.5 * d.lam_f[f] * d.fS[f];
     }
     double det = A00 * A11 - A01 * A01;
     double area = d.area[i];
@@ -234,7 +235,27 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
       d.grad[(2 * v + 1) * n + i] = b[2 * v + 1];
     }
     double phi[4] = {1.0, 1.0, 1.0, 1.0};
-    if (fl.limiter != 0) {
+    if (fl.limiter == 1) {
+      // Barth-Jespersen: the smallest ratio over the vertices comes from the largest
+      // excursion of each sign (correctly rounded division is monotone in the divisor),
+      // so two divisions per variable give the same bits as one per vertex
+      double up[4] = {0, 0, 0, 0}, dn[4] = {0, 0, 0, 0};
+      for (int k = d.cn_ptr[i]; k < d.cn_ptr[i + 1]; k++) {
+        int nd = d.cn_node[k];
+        double ox = d.xy[nd] - xi, oy = d.xy[d.nn + nd] - yi;
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+          double dv = b[2 * v] * ox + b[2 * v + 1] * oy;
+          up[v] = fmax(up[v], dv);
+          dn[v] = fmin(dn[v], dv);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 4; v++) {
+        if (up[v] > 0.0) phi[v] = fmin(phi[v], fmin(1.0, (wmax[v] - Wi[v]) / up[v]));
+        if (dn[v] < 0.0) phi[v] = fmin(phi[v], fmin(1.0, (wmin[v] - Wi[v]) / dn[v]));
+      }
+    } else if (fl.limiter == 2) {
       double h = sqrt(area);
       double eps2 = (fl.venkat_k * h) * (fl.venkat_k * h) * (fl.venkat_k * h);
       for (int k = d.cn_ptr[i]; k < d.cn_ptr[i + 1]; k++) {
@@ -244,10 +265,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
         for (int v = 0; v < 4; v++) {
           double dv = b[2 * v] * ox + b[2 * v + 1] * oy;
           double pv = 1.0;
-          if (fl.limiter == 1) {
-            if (dv > 0.0) pv = fmin(1.0, (wmax[v] - Wi[v]) / dv);
-            else if (dv < 0.0) pv = fmin(1.0, (wmin[v] - Wi[v]) / dv);
-          } else if (dv != 0.0) {
+          if (dv != 0.0) {
             double dp = dv > 0.0 ? wmax[v] - Wi[v] : wmin[v] - Wi[v];
             pv = ((dp * dp + eps2) * dv + 2.0 * dv * dv * dp) / (dv * (dp * dp + 2.0 * dv * dv + dv * dp + eps2));
           }
