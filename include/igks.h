@@ -139,10 +139,12 @@ int igks_set_flow(igks_ctx* ctx, int32_t solve, const igks_flow* f);
  * IGKS_EMESH if a cell has non-positive area or a face normal points into its left cell). */
 int igks_init_freestream(igks_ctx* ctx, int32_t solve);
 
-/* Advance every live solve by up to max_iters iterations. A solve stops on its own at
- * convergence (res_l2_rel <= res_target) or divergence. status (nullable) receives one
- * entry per solve. Returns IGKS_CONVERGED if every solve has converged, IGKS_OK if some
- * are still running, IGKS_DIVERGED if any diverged, or another error. */
+/* Advance every live solve by up to max_iters iterations: implicit (LU-SGS) or explicit
+ * (Eq. 15) per the solve's igks_flow.scheme. A solve stops on its own at convergence
+ * (res_l2_rel <= res_target, or the Eq. 40 ratio <= eq40_target when that is set) or
+ * divergence; the host checks every check_every iterations. status (nullable) receives
+ * one entry per solve. Returns IGKS_CONVERGED if every solve has converged, IGKS_OK if
+ * some are still running, IGKS_DIVERGED if any diverged, or another error. */
 int igks_iterate(igks_ctx* ctx, int32_t max_iters, igks_status* status);
 
 /* Enqueue n_iters iterations of every live solve on the context stream and return at
@@ -216,8 +218,8 @@ typedef struct igks_tuning {
   float ms_per_iter;       /* measured device time of one iteration with it */
 } igks_tuning;
 
-/* Time the library's launch configurations (sweep schedule and block size, flux block
- * size) on the context's live solves, iters_per_trial iterations each after one warm-up
+/* Time the library's launch configurations (sweep schedule, block size and blocks per
+ * solve, flux block size) on the context's live solves, iters_per_trial iterations each after one warm-up
  * iteration, and keep the fastest. Every trial starts from the same saved state and the
  * state is restored afterwards: the configurations do not change the arithmetic, so the
  * solves' iterates are exactly those of an untuned run. Allocates temporary device
