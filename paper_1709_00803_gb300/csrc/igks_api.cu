@@ -417,6 +417,7 @@ static int build(igks_ctx* ctx) {
   UP(ej_f, ej_f); UP(eslot_f, eslot_f); UP(ej_b, ej_b); UP(eslot_b, eslot_b);
   UP(cf_to_ef, cf_to_ef); UP(cf_to_eb, cf_to_eb);
   AL(rec_f, double, 13 * (size_t)P); AL(rec_b, double, 15 * (size_t)P);
+  AL(gprim, double, 6 * (size_t)nf);
   AL(ec_f, double, 4 * (size_t)PF_E * P); AL(ec_b, double, 4 * (size_t)PF_E * P);
   setup_sweeps();
   {
@@ -1032,8 +1033,8 @@ int igks_footprint_bytes(int32_t n_nodes, int32_t n_cells, int32_t n_faces, int3
   // per padded cell: 115 doubles (state, gradients, increments, sweep records) + 32 ints
   // (CSR pointers, orders, levels, positions, padded stencils); per CSR entry 60 B (face
   // and node lists, sweep stencil coefficients, maps) + 40 B (one sweep entry); per face
-  // 28 doubles + 8 ints; per node 2 doubles; a few hundred bytes per solve
-  *out = 1048 * ncp + 100 * (int64_t)nnz + 256 * (int64_t)n_faces + 16 * (int64_t)n_nodes + 4096;
+  // 34 doubles + 8 ints; per node 2 doubles; a few hundred bytes per solve
+  *out = 1048 * ncp + 100 * (int64_t)nnz + 304 * (int64_t)n_faces + 16 * (int64_t)n_nodes + 4096;
   return IGKS_OK;
 }
 

@@ -105,6 +105,7 @@ struct Dev {
   int npos;
   const int* pos_f; const int* pos_b;            // [nc_pad] position of a cell (-1 padding)
   void* rec_f;                                   // [13][P] T: M[5], r, mx, my, 1/D, 1/a_ii, u, v, H
+  void* gprim;                                   // [6][nf] T: ghost r, mx, my, u, v, H of wall/symmetry faces
   void* rec_b;                                   // [15][P] T: W[5], 1/D, 1/a_ii, u, v, H, dW*[5]
   void* ec_f; void* ec_b;                        // [4][PF_E][P] T: sx, sy, s lambda, SA coefficient
   const int* cnt_f; const int* ej_f; const int* eslot_f; const int* pb_of_pf;

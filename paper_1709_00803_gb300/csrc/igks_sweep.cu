@@ -137,6 +137,17 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_sweep_prep(Dev d) {
       T* o = (T*)d.ec_b;
       o[xb] = sc[k]; o[PE + xb] = sc[nnz + k]; o[2 * PE + xb] = sc[2 * nnz + k]; o[3 * PE + xb] = sc[3 * nnz + k];
     }
+    // the ghost state of a wall or symmetry face in the form the backward sweep's flux
+    // increment takes it (its only ghost entries), so the sweep itself does no FP64 work
+    const int bc = d.fbc[f];
+    if (j < 0 && (bc == 2 || bc == 3 || bc == 5)) {
+      const double gr = d.G[f], gmx = d.G[nf + f], gmy = d.G[2 * nf + f], gE = d.G[3 * nf + f];
+      const double gu = gmx / gr, gv = gmy / gr;
+      const double gp = (GAMMA - 1.0) * (gE - 0.5 * (gmx * gu + gmy * gv));
+      T* g = (T*)d.gprim;
+      g[f] = (T)gr; g[nf + f] = (T)gmx; g[2 * nf + f] = (T)gmy;
+      g[3 * nf + f] = (T)gu; g[4 * nf + f] = (T)gv; g[5 * nf + f] = (T)(gE + gp);
+    }
   }
 }
 
@@ -572,10 +583,9 @@ __device__ __forceinline__ void bwd_entry(const Dev& d, const T* ring, const T* 
       const T mn = ws[1] * fx + ws[2] * fy;
       w[1] = ws[1] - (T)2 * mn * fx; w[2] = ws[2] - (T)2 * mn * fy; w[4] = ws[4];
     }
-    const double gr = d.G[fc], gmx = d.G[nf + fc], gmy = d.G[2 * nf + fc], gE = d.G[3 * nf + fc];
-    const double gu = gmx / gr, gv = gmy / gr;
-    const double gp = (GAMMA - 1.0) * (gE - 0.5 * (gmx * gu + gmy * gv));
-    delta_flux<T>((T)gr, (T)gmx, (T)gmy, (T)gu, (T)gv, (T)(gE + gp), w[0], w[1], w[2], w[3], f);
+    const T* g = (const T*)d.gprim;   // ghost r, mx, my, u, v, H of this face (pre-pass)
+    delta_flux<T>(g[fc], g[nf + fc], g[2 * nf + fc], g[3 * nf + fc], g[4 * nf + fc], g[5 * nf + fc],
+                  w[0], w[1], w[2], w[3], f);
   }
   bwd_acc<T>(acc, sx, sy, sl, sa, f, w, sa_on);
 }
