@@ -370,9 +370,9 @@ def main():
     ap.add_argument("--explicit-cap", type=int, default=2000000, help="cavity: explicit iterations at most")
     ap.add_argument("--sweep-cluster", type=int, default=0,
                     help="blocks (thread-block cluster) per solve in the sweeps; 0: the library's choice")
-    ap.add_argument("--requests", type=int, default=16, help="requests of the serving workload")
+    ap.add_argument("--requests", type=int, default=12, help="requests of the serving workload")
     ap.add_argument("--cells-lo", type=int, default=2000)
-    ap.add_argument("--cells-hi", type=int, default=30000)
+    ap.add_argument("--cells-hi", type=int, default=12000)
     ap.add_argument("--slots", type=int, default=64, help="serving: live solves at most")
     ap.add_argument("--iters-per-step", type=int, default=100)
     ap.add_argument("--max-iters", type=int, default=20000)
