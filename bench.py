@@ -52,6 +52,10 @@ FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_GHZ / 1e3
 FLUX_FLOPS_PER_FACE = 3122.0
 # DRAM bytes (read + write) per face of one k_flux launch, from the same capture
 FLUX_DRAM_BYTES_PER_FACE = 188.1
+# DRAM bytes (read + write) per cell of one sweep launch on the turbulent plate, by sweep
+# type size (ncu: profiles/k_sweep_narrow_turbulent_plate.md, profiles/k_sweep_narrow_fp64_turbulent_plate.md)
+SWEEP_DRAM_BYTES_PER_CELL = {("k_sweep_fwd", 8): 279.1, ("k_sweep_bwd", 8): 296.2,
+                             ("k_sweep_fwd", 4): 162.7, ("k_sweep_bwd", 4): 170.4}
 
 
 def alg_bytes(kernel, t, nc, nf):
@@ -317,8 +321,9 @@ def rooflines(res, mesh, precision):
     dom = max(km, key=km.get)
     b = alg_bytes(dom, t, mesh.n_cells, mesh.n_faces)
     ach = b / (km[dom] / 1e3) / 1e9
+    per_cell = SWEEP_DRAM_BYTES_PER_CELL.get((dom, t))
     dominant = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "peak_source": f"hbm_gbs ({src}, burst copy)",
+                "traffic": per_cell * mesh.n_cells if per_cell else None, "peak_source": f"hbm_gbs ({src}, burst copy)",
                 "alg_bytes_per_launch": b, "note": "latency-bound dependency chain: one block walks the "
                 "sweep's levels; the HBM fraction shows how far it is from any bandwidth limit"}
     flux_t = km["k_flux"]
