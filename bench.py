@@ -4,6 +4,9 @@ both LU-SGS sweeps and the update) on a synthetic hybrid mesh.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl igks|reference]
                   [--precision fp64|mixed] [--workload turbulent_plate|laminar_plate|naca0012]
+  python bench.py --workload naca_batch   64 airfoil solves in one context (autotuned)
+  python bench.py --workload serving      request stream served vs the plain FP64 path
+  python bench.py --workload cavity       implicit vs explicit, Table 1 vortex centres
 
 One step = one iteration of the whole hot path over one steady solve of the workload.
 `value` is device time (CUDA events on the library's stream around each step, L2 flushed
