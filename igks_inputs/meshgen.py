@@ -194,7 +194,8 @@ def flat_plate_quads(nx: int = 64, ny: int = 32, ratio: float = 1.1,
 
     x uniform on [xmin, xmax]; y geometric with `ratio` on [0, height] (or with the
     given first spacing, the ratio then solved so the layer reaches `height`).
-    Wall on y = 0 for x >= 0, symmetry on y = 0 for x < 0, far field elsewhere."""
+    Wall on y = 0 for x >= 0, symmetry on y = 0 for x < 0, free stream at the inflow (left),
+    outflow on the upper and right boundaries."""
     xs = np.linspace(xmin, xmax, nx + 1)
     if first is None:
         first = height * (ratio - 1.0) / (ratio ** ny - 1.0) if ratio != 1.0 else height / ny
