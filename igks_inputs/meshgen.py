@@ -13,7 +13,8 @@ A mesh is returned as plain numpy arrays in the face/cell layout the C ABI takes
                                          left cell, so the right-hand normal of a->b
                                          points out of the left cell
     face_cells  int32   [n_faces, 2]     (left, right); right = -1 on a boundary face
-    face_bc     int32   [n_faces]        0 interior, 1 far field, 2 symmetry, 3 wall
+    face_bc     int32   [n_faces]        0 interior, 1 free stream, 2 symmetry, 3 wall, 4 outflow,
+                                         5 moving wall
 
 Faces are numbered in the order they are first met while scanning cells in order and,
 inside a cell, its edges in counter-clockwise order. Cells keep the generator's order;
@@ -459,7 +460,7 @@ def naca_omesh(m: float = 0.0, p: float = 0.0, t: float = 0.12, n_around: int = 
 def tiny_quads(nx: int = 2, ny: int = 2, skew: float = 0.0, seed: int = 0,
                bcs=("wall", "farfield")) -> Mesh:
     """nx x ny quads on [0,1]^2 (optionally with jittered interior nodes). Bottom edge
-    is wall (or symmetry), the rest far field."""
+    is wall (or symmetry), the rest free stream (or as bcs[1] says)."""
     rng = np.random.default_rng(seed)
     xs = np.linspace(0.0, 1.0, nx + 1)
     ys = np.linspace(0.0, 1.0, ny + 1)
@@ -481,7 +482,7 @@ def tiny_quads(nx: int = 2, ny: int = 2, skew: float = 0.0, seed: int = 0,
 
 
 def triangle_fan(n: int = 4, radius: float = 1.0) -> Mesh:
-    """n triangles around a centre node; the outer edges are far field."""
+    """n triangles around a centre node; the outer edges are free stream."""
     ang = np.linspace(0.0, 2 * math.pi, n, endpoint=False) + 0.3
     xy = np.concatenate([[[0.0, 0.0]], np.stack([radius * np.cos(ang), radius * np.sin(ang)], 1)])
     cells = [[0, 1 + k, 1 + (k + 1) % n] for k in range(n)]

@@ -220,7 +220,8 @@ __global__ void __launch_bounds__(128) k_flux(Dev d) {
     rot(stt, nx, ny, SLt);
     rot(WcLg, nx, ny, WcL);
   }
-  // ---- right side: interior cell, mirrored ghost (wall, symmetry) or far-field ghost ----
+  // ---- right side: interior cell, mirrored ghost (wall, symmetry, moving wall) or the
+  //      free-stream / outflow ghost state without slopes ----
   double WcRg[5], WcR[4], WR[4], SRn[4], SRt[4];
   double muR, mtR;
   if (R >= 0) {

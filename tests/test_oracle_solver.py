@@ -1,7 +1,7 @@
 """Pins of the oracle's whole iteration against invariants and independent solves.
 
   * geometry: cells close (sum n S = 0), areas add up to the domain,
-  * free stream is preserved to round-off on an all-far-field mesh (Section II.E),
+  * free stream is preserved to round-off on a mesh closed by free-stream faces (Section II.E),
   * discrete conservation: interior face fluxes telescope (Eq. 15-16),
   * the two LU-SGS sweeps equal a dense direct solve of the factored system
     (L + D) D^-1 (D + U) dW = M of Eq. 22, the blocks built from the textbook Euler
