@@ -66,6 +66,7 @@ def lib():
         L.ora_face_flux.argtypes = [P(OraFlow)] + [dp] * 8 + [d, d, d, d, dp, dp]
         L.ora_face_flux.restype = i
         L.ora_euler_flux.argtypes = [dp, d, d, dp]
+        L.ora_sa_source.argtypes = [d, d, d, d, dp]
         L.ora_create.argtypes = [i, dp, i, ip, ip, i, ip, ip, ip, P(OraFlow)]
         L.ora_create.restype = C.c_void_p
         L.ora_destroy.argtypes = [C.c_void_p]
@@ -135,6 +136,14 @@ def viscosity(flow, lam):
 def euler_flux(W, nx, ny):
     W = np.ascontiguousarray(W[:4], dtype=np.float64); F = np.zeros(4)
     lib().ora_euler_flux(_dp(W), nx, ny, _dp(F)); return F
+
+
+def sa_source(nut, nu, omega, d):
+    """Spalart-Allmaras source of Eq. 28a per unit volume and its parts:
+    dict(Sr, fw, S_tilde, r, fv1, fv2)."""
+    o = np.zeros(6)
+    lib().ora_sa_source(nut, nu, omega, d, _dp(o))
+    return dict(zip(("Sr", "fw", "S_tilde", "r", "fv1", "fv2"), o.tolist()))
 
 
 def face_flux(flow, WL, WR, sLn, sLt, sRn, sRt, WcL, WcR, dL, dR, mut, dt):

@@ -913,9 +913,32 @@ static int step_fluxes(ora_solver* s) {
   return 0;
 }
 
+/* Spalart-Allmaras source of Eq. 28a per unit volume, Sr = cb1 S~ nu~ - cw1 fw (nu~/d)^2
+ * (SA-noft2; S~ with the 2012 clipping), for nu~ = nut, laminar kinematic viscosity nu,
+ * vorticity magnitude omega and wall distance d. out: Sr, fw, S~, r, fv1, fv2. */
+void ora_sa_source(double nut, double nu, double om, double d, double* out) {
+  const double cv1 = SA_CV1, k2 = SA_KAPPA * SA_KAPPA;
+  double chi = nut / nu, c3 = chi * chi * chi;
+  double fv1 = c3 / (c3 + cv1 * cv1 * cv1);
+  double fv2 = 1.0 - chi / (1.0 + chi * fv1);
+  double Sbar = nut * fv2 / (k2 * d * d);
+  double St;
+  if (Sbar >= -SA_CV2 * om) St = om + Sbar;
+  else St = om + om * (SA_CV2 * SA_CV2 * om + SA_CV3 * Sbar) / ((SA_CV3 - 2.0 * SA_CV2) * om - Sbar);
+  double rr = (nut < 10.0 * St * k2 * d * d) ? nut / (St * k2 * d * d) : 10.0;
+  double gg = rr + SA_CW2 * (pow(rr, 6.0) - rr);
+  double c6 = pow(SA_CW3, 6.0);
+  double fw = gg * pow((1.0 + c6) / (pow(gg, 6.0) + c6), 1.0 / 6.0);
+  out[0] = SA_CB1 * St * nut - SA_CW1 * fw * (nut / d) * (nut / d);
+  out[1] = fw;
+  out[2] = St;
+  out[3] = rr;
+  out[4] = fv1;
+  out[5] = fv2;
+}
+
 /* ---- step 5: residual M (Eq. 16) and the SA right-hand side (Eq. 27-28a) ---- */
 static void step_residual(ora_solver* s) {
-  const double cv1 = SA_CV1, k2 = SA_KAPPA * SA_KAPPA;
   for (int i = 0; i < s->n_cells; i++) {
     double acc[5] = {0, 0, 0, 0, 0};
     for (int k = s->cf_ptr[i]; k < s->cf_ptr[i + 1]; k++) {
@@ -935,27 +958,15 @@ static void step_residual(ora_solver* s) {
     s->fw[i] = 0.0;
     if (s->flow.sa_on) {
       const double* Wi = s->W + 5 * i;
-      double nut = Wi[4], rho = Wi[0], u = Wi[1] / rho, v = Wi[2] / rho;
-      double nu = nu_lam(s, Wi);
-      double chi = nut / nu, c3 = chi * chi * chi;
-      double fv1 = c3 / (c3 + cv1 * cv1 * cv1);
-      double fv2 = 1.0 - chi / (1.0 + chi * fv1);
+      double rho = Wi[0], u = Wi[1] / rho, v = Wi[2] / rho;
       const double* g = s->grad + 8 * i;
       double dudy = (g[3] - u * g[1]) / rho;
       double dvdx = (g[4] - v * g[0]) / rho;
       double om = fabs(dvdx - dudy);
-      double d = s->wall_d[i];
-      double Sbar = nut * fv2 / (k2 * d * d);
-      double St;
-      if (Sbar >= -SA_CV2 * om) St = om + Sbar;
-      else St = om + om * (SA_CV2 * SA_CV2 * om + SA_CV3 * Sbar) / ((SA_CV3 - 2.0 * SA_CV2) * om - Sbar);
-      double rr = (nut < 10.0 * St * k2 * d * d) ? nut / (St * k2 * d * d) : 10.0;
-      double gg = rr + SA_CW2 * (pow(rr, 6.0) - rr);
-      double c6 = pow(SA_CW3, 6.0);
-      double fw = gg * pow((1.0 + c6) / (pow(gg, 6.0) + c6), 1.0 / 6.0);
-      double Sr = SA_CB1 * St * nut - SA_CW1 * fw * (nut / d) * (nut / d);
-      s->fw[i] = fw;
-      Mi[4] = s->area[i] * Sr + acc[4];
+      double src[6];
+      ora_sa_source(Wi[4], nu_lam(s, Wi), om, s->wall_d[i], src);
+      s->fw[i] = src[1];
+      Mi[4] = s->area[i] * src[0] + acc[4];
     }
   }
 }
@@ -975,7 +986,11 @@ static void step_norms(ora_solver* s) {
     s->cfl = s->flow.cfl_init;
     s->res_l2_first = s->res_l2;
   } else {
-    double c = s->cfl * s->res_inf_prev / s->res_inf;
+    /* Eq. 25; a residual that vanished exactly makes the ratio infinite (CFL to its cap),
+     * and two vanishing residuals in a row leave the CFL unchanged */
+    double c;
+    if (s->res_inf > 0.0) c = s->cfl * s->res_inf_prev / s->res_inf;
+    else c = (s->res_inf_prev > 0.0) ? s->flow.cfl_max : s->cfl;
     if (c < s->flow.cfl_min) c = s->flow.cfl_min;
     if (c > s->flow.cfl_max) c = s->flow.cfl_max;
     s->cfl = c;
@@ -1130,7 +1145,9 @@ int ora_iterate(ora_solver* s, int n_iter) {
     step_update(s);
     s->iter++;
     if (s->status < 0) return s->status;
-    if ((s->res_l2_first > 0.0 && s->res_l2 <= s->flow.res_target * s->res_l2_first) ||
+    /* converged when the density residual fell to res_target times its first value; a
+     * residual that is exactly zero (also at the first iteration) has nothing left to fall */
+    if ((s->res_l2 <= s->flow.res_target * s->res_l2_first) ||
         (s->flow.eq40_target > 0.0 && s->eq40 <= s->flow.eq40_target)) {
       s->status = 1;
       return 1;

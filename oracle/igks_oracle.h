@@ -39,6 +39,8 @@ int  ora_face_flux(const ora_flow* f, const double* WL, const double* WR,
                    const double* WcL, const double* WcR, double dL, double dR,
                    double mut_face, double dt, double* F /*[4]*/, double* heat /*[1] or NULL*/);
 void ora_euler_flux(const double* W, double nx, double ny, double* F /*[4]*/);
+void ora_sa_source(double nut, double nu, double omega, double d,
+                   double* out /*[6]: Sr, fw, S_tilde, r, fv1, fv2*/);
 
 /* --- whole solver --- */
 ora_solver* ora_create(int n_nodes, const double* xy, int n_cells, const int* cell_ptr,

@@ -401,11 +401,17 @@ __global__ void k_norms(Dev d) {
     st.cfl = fl.cfl_init;
     st.res_l2_first = st.res_l2;
   } else {
-    double c = st.cfl * st.res_inf_prev / st.res_inf;
+    // Eq. 25; a residual that vanished exactly makes the ratio infinite (CFL to its cap),
+    // two vanishing residuals in a row leave the CFL unchanged
+    double c;
+    if (st.res_inf > 0.0) c = st.cfl * st.res_inf_prev / st.res_inf;
+    else c = (st.res_inf_prev > 0.0) ? fl.cfl_max : st.cfl;
     st.cfl = fmin(fmax(c, fl.cfl_min), fl.cfl_max);
   }
   st.res_inf_prev = st.res_inf;
-  st.pending = (st.res_l2_first > 0.0 && st.res_l2 <= fl.res_target * st.res_l2_first) ? 1 : 0;
+  // converged at res_target times the first residual; an exactly zero residual (also at the
+  // first iteration) has nothing left to fall
+  st.pending = (st.res_l2 <= fl.res_target * st.res_l2_first) ? 1 : 0;
 }
 
 void launch_norms(const Dev& d, cudaStream_t s) {

@@ -391,3 +391,48 @@ def test_moving_wall_ghost_mirrors_velocity_about_the_lid():
         np.testing.assert_allclose(u, u_ghost, rtol=1e-14, atol=1e-14)
         np.testing.assert_allclose(v, 0.0, atol=1e-14)
         np.testing.assert_allclose(p, 1.02 * p0, rtol=1e-13)
+
+
+@pytest.mark.parametrize("ratio", [1e3, 1e5])
+def test_flux_ns_limit_shear_through_the_tangential_slopes(ratio):
+    """U_n = a x_t (the normal velocity varies along the face): the shear stress
+    mu (dU_t/dn + dU_n/dt) = mu a is carried by the tangential slopes a_t and abar_t of
+    Eq. 4-5 alone, so the tangential momentum flux tends to -mu a dt as tau/dt -> 0. The
+    flow is divergence free and steady at the face: no other flux changes."""
+    fl = _flow(reynolds=1e3)
+    rho, p, a = 1.0, 1 / (GAM * fl.mach ** 2), 0.8
+    lam = rho / (2 * p)
+    mu = _sutherland(fl, lam)
+    dt = ratio * mu / p
+    W = _cons(rho, 0.0, 0.0, p)
+    st = np.array([0.0, rho * a, 0.0, 0.0])     # d(rho U_n)/dt; U_n = 0 at the face
+    z = np.zeros(4)
+    Fx, _ = O.face_flux(fl, W, W, z, st, z, st, W, W, 1e-3, 1e-3, 0.0, dt)
+    ref = -mu * a * dt
+    assert abs(Fx[2] - ref) <= 5.0 / ratio * abs(ref) + 1e-12 * abs(ref)
+    assert abs(Fx[1] - p * dt) <= 5.0 / ratio * abs(ref) + 1e-13 * p * dt
+    assert abs(Fx[0]) <= 1e-10 * abs(ref) and abs(Fx[3]) <= 1e-10 * abs(ref)
+
+
+@pytest.mark.parametrize("ratio", [1e3, 1e4])
+def test_flux_ns_limit_normal_stress(ratio):
+    """U_n = a x_n at uniform density and pressure: the BGK normal stress of a gas with
+    D = K + 2 energy-carrying degrees of freedom is -2 mu a (D - 1)/D (Chapman-Enskog of
+    Eq. 1; 1.6 mu a here), on top of the pressure, which itself evolves by the Euler
+    equations, dp/dt = -a p (D + 2)/D at the face, over the step: the normal momentum flux
+    tends to p dt - a p (D + 2)/D dt^2/2 - 2 mu a (D - 1)/D dt."""
+    fl = _flow(reynolds=1e3)
+    rho, p, a = 1.0, 1 / (GAM * fl.mach ** 2), 0.05
+    lam = rho / (2 * p)
+    mu = _sutherland(fl, lam)
+    dt = ratio * mu / p
+    D = K + 2
+    d = 1e-7          # centre states close to the face: their kinetic energy is O(a^2 d^2)
+    W = _cons(rho, 0.0, 0.0, p)
+    sn = np.array([0.0, rho * a, 0.0, 0.0])
+    z = np.zeros(4)
+    Fx, _ = O.face_flux(fl, W, W, sn, z, sn, z, _cons(rho, -a * d, 0.0, p), _cons(rho, a * d, 0.0, p), d, d, 0.0, dt)
+    stress = -2.0 * mu * a * (D - 1) / D * dt
+    ref = p * dt - a * p * (D + 2) / D * dt * dt / 2 + stress
+    assert abs(Fx[1] - ref) <= 10.0 / ratio * abs(stress) + 1e-13 * p * dt, (Fx[1] - ref) / stress
+    assert abs(Fx[0]) <= 1e-10 * abs(stress) and abs(Fx[2]) <= 1e-10 * abs(stress)

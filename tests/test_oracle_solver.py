@@ -243,3 +243,127 @@ def test_wall_ghost_face_velocity_zero():
     # symmetry faces of the plate are horizontal: normal momentum (y) flips
     ls = m.face_cells[sym, 0]
     assert np.allclose(gh[2, sym], -W[2, ls]) and np.allclose(gh[1, sym], W[1, ls])
+
+
+def _venkat_phi(k, A=0.06):
+    """Density limiter factor of the centre cell of a 3 x 3 box of unit-spaced quads whose
+    density columns hold rho0 - A, rho0, rho0 + A/3: the least-squares slope is 2A/3 per
+    cell, so the vertex excursions are +-A/3 against a neighbourhood range of +A/3 / -A."""
+    m = G.tiny_quads(3, 3, bcs=("symmetry", "symmetry"))
+    fl = F.laminar_plate_flow()
+    fl.limiter = F.LIMITER_VENKAT
+    fl.venkat_k = k
+    W = F.uniform_state(m, fl)
+    col = np.arange(m.n_cells) % 3
+    W[0] = 1.0 + np.array([-A, 0.0, A / 3.0])[col]
+    o = O.Oracle(m, fl)
+    o.set_W(W)
+    o.iterate(1)
+    return o.get(O.ORA_PHI)
+
+
+def test_venkatakrishnan_limiter_values_and_limits():
+    """Venkatakrishnan's smooth limiter at the excursion ratio y = range / excursion: with
+    K = 0 it is (y^2 + 2y)/(y^2 + y + 2), which is 3/4 at y = 1 and exceeds 1 only for y > 2
+    (the factor is capped at 1); as K grows it tends to 1 (no limiting)."""
+    phi = _venkat_phi(0.0)
+    assert abs(phi[0, 4] - 0.75) <= 1e-14
+    assert np.all(phi[1:, 4] == 1.0)               # uniform momentum and energy
+    ks = [0.0, 0.5, 1.0, 3.0, 30.0]
+    vals = [_venkat_phi(k)[0, 4] for k in ks]
+    assert all(a < b for a, b in zip(vals, vals[1:]))
+    assert 1.0 - vals[-1] < 1e-4
+
+
+def test_venkatakrishnan_factors_stay_in_zero_one():
+    m = G.flat_plate_hybrid(nx=20, nq=6, ntri_rows=6, first=1e-3, seed=4)
+    fl = F.laminar_plate_flow()
+    fl.limiter = F.LIMITER_VENKAT
+    for k in (0.0, 0.3, 5.0):
+        fl.venkat_k = k
+        o = O.Oracle(m, fl)
+        W = F.perturbed_state(m, fl, seed=6, amp=0.2)
+        W[0, 50] *= 1.5
+        o.set_W(W)
+        o.iterate(1)
+        phi = o.get(O.ORA_PHI)
+        assert phi.min() >= 0.0 and phi.max() <= 1.0
+        if k == 0.0:
+            assert phi[0, 50] < 0.5          # the local extremum is limited
+
+
+def test_viscous_spectral_radius_closed_form():
+    """Two cells side by side: lambda_f = |Vbar . n| + cbar + 2 (mubar + mutbar) gamma /
+    (rhobar Pr dn), with the means over the two cells (reading (ii) of the spectral radius
+    of Eq. 20-21), Sutherland's law for mu and mu_t = rho nu~ fv1."""
+    xy = np.array([[0, 0], [1, 0], [2, 0], [0, 0.5], [1, 0.5], [2, 0.5]], dtype=np.float64)
+    m = G.build_mesh(xy, [[0, 1, 4, 3], [1, 2, 5, 4]], lambda a, b, xm, ym: G.BC_FARFIELD, name="two_cells")
+    fl = F.turbulent_plate_flow()
+    fl.reynolds = 300.0
+    W = np.zeros((5, 2))
+    prim = [(1.1, 0.7, -0.2, 19.0, 0.02), (0.9, 0.4, 0.3, 16.0, 0.05)]
+    for c, (r, u, v, p, nut) in enumerate(prim):
+        W[:, c] = [r, r * u, r * v, p / (GAM - 1) + 0.5 * r * (u * u + v * v), nut]
+    o = O.Oracle(m, fl)
+    o.set_W(W)
+    o.iterate(1)
+    lam = o.get(O.ORA_LAMBDA_F)
+    f = int(np.nonzero(m.face_cells[:, 1] >= 0)[0][0])
+    n = np.array([1.0, 0.0]) if m.face_cells[f, 0] == 0 else np.array([-1.0, 0.0])
+    p_inf = 1 / (GAM * fl.mach ** 2)
+    s = fl.s_suth / fl.t_ref
+    mus, muts = [], []
+    for (r, u, v, p, nut) in prim:
+        tr = (p / r) / p_inf                          # T / T_inf
+        mu = (1 / fl.reynolds) * tr ** 1.5 * (1 + s) / (tr + s)
+        chi3 = (nut * r / mu) ** 3
+        mus.append(mu)
+        muts.append(r * nut * chi3 / (chi3 + 7.1 ** 3))
+    (r0, u0, v0, p0, _), (r1, u1, v1, p1, _) = prim
+    vbar = 0.5 * np.array([u0 + u1, v0 + v1])
+    cbar = 0.5 * (math.sqrt(GAM * p0 / r0) + math.sqrt(GAM * p1 / r1))
+    ref = abs(vbar @ n) + cbar + 2 * (0.5 * sum(mus) + 0.5 * sum(muts)) * GAM / (0.5 * (r0 + r1) * fl.prandtl * 1.0)
+    assert abs(lam[f] - ref) <= 1e-13 * ref
+    fl.visc_sr = 0
+    o2 = O.Oracle(m, fl)
+    o2.set_W(W)
+    o2.iterate(1)
+    assert abs(o2.get(O.ORA_LAMBDA_F)[f] - (abs(vbar @ n) + cbar)) <= 1e-14 * ref
+
+
+def test_exactly_zero_residual_counts_as_converged():
+    """Fluid at rest in a box closed by symmetry planes on an axis-aligned mesh: every face
+    carries the pressure alone and each cell's fluxes cancel exactly, so the residual is
+    exactly zero. The solve stops at once as converged and the CFL stays finite."""
+    m = G.tiny_quads(6, 4, bcs=("symmetry", "symmetry"))
+    fl = F.cavity_flow()
+    o = O.Oracle(m, fl)
+    o.set_W(F.rest_state(m, fl))
+    assert o.iterate(5) == 1
+    sc = o.scalars()
+    assert sc["iter"] == 1 and sc["res_l2"] == 0.0 and sc["res_inf"] == 0.0
+    assert math.isfinite(sc["cfl"]) and sc["cfl"] == fl.cfl_init
+
+
+def test_zero_residual_after_a_nonzero_one_sends_the_cfl_to_its_cap():
+    """Eq. 25 with a residual that vanished exactly: the ratio of the norms is infinite, so
+    the CFL goes to its cap; after two vanishing residuals in a row it stays put."""
+    m = G.tiny_quads(6, 4, bcs=("symmetry", "symmetry"))
+    fl = F.cavity_flow()
+    for prev, cfl_expected in ((3.5, fl.cfl_max), (0.0, 2345.0)):
+        o = O.Oracle(m, fl)
+        o.set_W(F.rest_state(m, fl))
+        o.set_scalars({"iter": 7, "cfl": 2345.0, "res_inf_prev": prev, "res_l2_first": 1.0})
+        assert o.iterate(1) == 1
+        sc = o.scalars()
+        assert sc["res_inf"] == 0.0 and sc["cfl"] == cfl_expected
+
+
+def test_venkatakrishnan_epsilon_is_k_h_cubed():
+    """Venkatakrishnan's threshold eps^2 = (K h)^3 with h = sqrt(Omega): at the excursion
+    ratio y = 1 the factor is (3 d^2 + eps^2) / (4 d^2 + eps^2), d the vertex excursion
+    (A/3 = 0.02 here, h = 1/3)."""
+    d2 = 0.02 ** 2
+    for k in (0.3, 0.5, 1.0):
+        e2 = (k / 3.0) ** 3
+        assert abs(_venkat_phi(k)[0, 4] - (3 * d2 + e2) / (4 * d2 + e2)) <= 1e-13
