@@ -1,22 +1,25 @@
 """Benchmark of the IGKS hot path on GB300: cell-updates/s of full implicit iterations
 (ghosts, spectral radius, gradients, gas-kinetic flux with SA terms, residual, norms,
-both LU-SGS sweeps and the update) on a synthetic hybrid mesh.
+both LU-SGS sweeps and the update).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl igks|reference]
-                  [--precision fp64|mixed] [--workload turbulent_plate|laminar_plate|naca0012]
-  python bench.py --workload naca_batch   64 airfoil solves in one context (autotuned)
+      default: the 64-airfoil batch (64 seeded NACA 4-digit sections, SA, O-meshes of
+      8k-80k cells, 2.26M cells in one context, FP32 sweeps with FP64 flux, residual and
+      update, autotuned launch configuration), with the turbulent flat plate (FP64 and
+      FP32 sweeps) and a bounded serving leg (converged solves/hour, p50/p99) beside it
+  python bench.py --workload turbulent_plate|laminar_plate|naca0012 [--precision fp64|mixed]
   python bench.py --workload serving      request stream served vs the plain FP64 path
   python bench.py --workload cavity       implicit vs explicit, Table 1 vortex centres
 
-One step = one iteration of the whole hot path over one steady solve of the workload.
+One step = one iteration of the whole hot path over every solve of the workload.
 `value` is device time (CUDA events on the library's stream around each step, L2 flushed
-between steps by writing a 256 MiB buffer outside the timed intervals) for the headline
-precision; the other precision is measured the same way and reported under "other".
-`e2e` is the same metric through the public API with host buffers: each step copies the
-state in from pinned host memory, iterates once (reading the per-solve status back) and
-copies the state out. Under torchrun each rank runs an independent replica (the method
-does not shard: replicas only) and rank 0 prints one JSON line with the max time over
-ranks. --impl reference times the CPU oracle (single thread) on the same workload.
+between steps by writing a 256 MiB buffer outside the timed intervals). `e2e` is the same
+metric through the public API with host buffers: each step copies every solve's state in
+from pinned host memory, iterates once (reading the per-solve status back) and copies the
+states out. Under torchrun each rank runs an independent replica (the method does not
+shard: replicas only) and rank 0 prints one JSON line with the max time over ranks.
+--impl reference times the CPU oracle (single thread) on a bounded sample of the same
+workload.
 """
 from __future__ import annotations
 
@@ -45,20 +48,26 @@ WORKLOADS = {
     "naca0012": (G.naca0012, F.naca_flow, "NACA 0012, SA, Ma 0.15, Re 6e6, AoA 10, hybrid O-mesh"),
 }
 METRIC = "cell-updates/s"
-SM_COUNT, SM_MAX_GHZ = 152, 2.07
-# FP64 peak derived from unit counts and clock: 2 FP64 FMA per SM per clock (1.25 TFLOP/s
-# nominal) x 2 flop x 152 SMs x 2.07 GHz
-FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_GHZ / 1e3
-# Executed FP64 flops per face of k_flux (2 x DFMA + DADD + DMUL from ncu on the turbulent
-# plate, 35056 faces, profiles/k_flux_turbulent_plate.md): the per-unit figure of its ALU
-# roofline
-FLUX_FLOPS_PER_FACE = 3122.0
-# DRAM bytes (read + write) per face of one k_flux launch, from the same capture
-FLUX_DRAM_BYTES_PER_FACE = 188.1
-# DRAM bytes (read + write) per cell of one sweep launch on the turbulent plate, by sweep
-# type size (ncu: profiles/k_sweep_narrow_turbulent_plate.md, profiles/k_sweep_narrow_fp64_turbulent_plate.md)
-SWEEP_DRAM_BYTES_PER_CELL = {("k_sweep_fwd", 8): 279.1, ("k_sweep_bwd", 8): 296.2,
-                             ("k_sweep_fwd", 4): 162.7, ("k_sweep_bwd", 4): 170.4}
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0
+# FP64 units of GB300: 2 FP64 FMA per SM per clock (1.25 TFLOP/s nominal at 2.07 GHz); the
+# ALU peak of the flux kernel is this count at the SM clock sampled during the run
+FP64_FLOP_PER_SM_CLK = 4.0
+# Algorithmic FP64 work of the gas-kinetic flux per face: 2 kflop, the upper end of the
+# method's own count (two erfc/exp pairs, ten 4x4 moment solves, the moment tables to
+# order 6-7 and the flux assembly); what the kernel executes on top (the instructions
+# inside the library's erfc/exp/divide) does not count as work done
+FLUX_ALG_FLOPS_PER_FACE = 2000.0
+# ncu figures per face / per cell of one launch, by workload, with the capture they come
+# from (executed FP64 flops = 2 x DFMA + DADD + DMUL thread instructions; DRAM = read +
+# write bytes). None: not captured for that workload.
+NCU = {
+    "naca_batch": {"source": "ncu, k_flux on an 8-airfoil slice of the 64-airfoil batch",
+                   "flux_exec_flops_per_face": None, "flux_dram_bytes_per_face": None},
+    "turbulent_plate": {"source": "ncu, k_flux and the narrow sweeps on the turbulent flat plate (35056 faces)",
+                        "flux_exec_flops_per_face": 3122.0, "flux_dram_bytes_per_face": 188.1,
+                        "sweep_dram_bytes_per_cell": {("k_sweep_fwd", 8): 279.1, ("k_sweep_bwd", 8): 296.2,
+                                                      ("k_sweep_fwd", 4): 162.7, ("k_sweep_bwd", 4): 170.4}},
+}
 
 
 def alg_bytes(kernel, t, nc, nf):
@@ -199,6 +208,54 @@ def run_reference(args, mesh, flow, desc, budget_s=150.0):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_batch(args, budget_s=150.0):
+    """The reference arm on the batch workload: the CPU oracle, single-threaded. One step
+    is one oracle iteration of one airfoil of the batch (airfoil k mod 64 at step k, from
+    the free stream); value = cells iterated / time. The steps are capped so that the run
+    stays within about budget_s seconds; the sample actually timed is stated."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    import oracle as O
+    cases = batch_cases(args.batch)
+    oras = {}
+
+    def step(k):
+        m, fl = cases[k % len(cases)]
+        if k % len(cases) not in oras:
+            oras[k % len(cases)] = O.Oracle(m, fl)
+        oras[k % len(cases)].iterate(1)
+        return m.n_cells
+
+    t_start = time.perf_counter()
+    for k in range(args.warmup):
+        step(k)
+        if time.perf_counter() - t_start > 0.2 * budget_s:
+            break
+    t0 = time.perf_counter()
+    cells, n = 0, 0
+    for k in range(args.steps):
+        cells += step(args.warmup + k)
+        n += 1
+        if time.perf_counter() - t0 > 0.8 * budget_s:
+            break
+    dt = time.perf_counter() - t0
+    v = cells / dt
+    sample = (f"{n} timed steps (of --steps {args.steps}), each one oracle iteration of one airfoil of the "
+              f"64-airfoil batch in turn ({cells} cell-updates), after {args.warmup} warm-up steps, "
+              f"single-threaded C oracle")
+    desc = (f"{len(cases)} seeded NACA 4-digit airfoils (m 0-0.06, p 0.2-0.6, t 0.08-0.18), Ma 0.1-0.75, "
+            f"AoA -4..8 deg, Re_c 1e6-1e7, SA, hybrid O-meshes of 8k-80k cells in one context")
+    line = {"metric": METRIC, "value": v, "unit": METRIC, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(n, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "solves": len(cases),
+                                            "cells": sum(m.n_cells for m, _ in cases),
+                                            "faces": sum(m.n_faces for m, _ in cases), "precision": "fp64"},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def measure(args, mesh, flow, precision, dev, dist, ws, with_e2e):
     """Time args.steps iterations of one solve at one sweep precision."""
     import torch
@@ -263,7 +320,7 @@ def measure(args, mesh, flow, precision, dev, dist, ws, with_e2e):
     return res
 
 
-def measure_batch(args, cases, precision, dev, dist, ws):
+def measure_batch(args, cases, precision, dev, dist, ws, with_e2e=False):
     """Time args.steps iterations of many solves in one context (one launch per kernel
     covers every solve); only cells of solves still running count as updated."""
     import torch
@@ -281,63 +338,109 @@ def measure_batch(args, cases, precision, dev, dist, ws):
     ncells = np.array([m.n_cells for m, _ in cases])
     ctx.enqueue(args.warmup)
     stream.synchronize()
-    tuning = ctx.autotune(3)          # launch configuration for this batch (state restored)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")
-    ktimes, step_ms, live_cells = {}, [], []
+    tuning = ctx.autotune(5)          # launch configuration for this batch (state restored)
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     _, st = ctx.iterate(0)
+    it0 = np.array([q["iters"] for q in st])
+    live0 = int(ncells[np.array([q["state"] == 0 for q in st])].sum())
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    # the K steps as one window: the groups of solves run on streams of their own and drift
+    # against each other, so that one group's sweeps overlap another's flux; the state and
+    # mesh data of a step (2+ GB) are far larger than the 129 MB L2, so nothing is flushed
     with ClockSampler(dev) as clk:
-        for k in range(args.steps):
-            live = np.array([q["state"] == 0 for q in st])
-            with torch.cuda.stream(stream):
-                flush.fill_(float(k))
-            s0.record(stream)
-            ctx.enqueue(1)
-            s1.record(stream)
-            stream.synchronize()
-            step_ms.append(s0.elapsed_time(s1))
-            live_cells.append(int(ncells[live].sum()))
-            for name, t in ctx.kernel_times().items():
-                ktimes.setdefault(name, []).append(t)
-            _, st = ctx.iterate(0)
-    total_ms = float(sum(step_ms))
-    total_ms = _max_over_ranks(dist, total_ms, f"cuda:{dev}")
+        s0.record(stream)
+        ctx.enqueue(args.steps)
+        s1.record(stream)
+        stream.synchronize()
+    total_ms = _max_over_ranks(dist, float(s0.elapsed_time(s1)), f"cuda:{dev}")
+    _, st = ctx.iterate(0)
+    updates = int((ncells * (np.array([q["iters"] for q in st]) - it0)).sum())
     states = [q["state"] for q in st]
-    res = {"value": ws * sum(live_cells) / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+    # the per-kernel split, one group (the kernels one after another), a few more iterations
+    ctx.set_launch(dict(tuning, groups=1))
+    ktimes = {}
+    for _ in range(3):
+        ctx.enqueue(1)
+        stream.synchronize()
+        for name, t in ctx.kernel_times().items():
+            ktimes.setdefault(name, []).append(t)
+    ctx.set_launch(tuning)
+    res = {"value": ws * updates / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
            "kernel_ms": {k: round(statistics.mean(v), 5) for k, v in ktimes.items()},
+           "kernel_ms_note": "one group, the kernels in sequence, 3 iterations after the timed window",
            "launches_per_step": ctx.launches_per_iteration(), "clocks": clk.summary(),
            "solves": len(cases), "running": states.count(0), "converged": states.count(1),
-           "diverged": sum(1 for x in states if x < 0), "live_cells_first_last": [live_cells[0], live_cells[-1]],
+           "diverged": sum(1 for x in states if x < 0), "live_cells_first_last": [live0, int(ncells[np.array([x == 0 for x in states])].sum())],
            "autotune": tuning}
+    if with_e2e:
+        # every solve's state in from pinned host memory, one iteration through the public
+        # API (igks_iterate reads the per-solve status back), every state out again
+        hosts = [torch.empty((5, m.n_cells), dtype=torch.float64).pin_memory().numpy() for m, _ in cases]
+        for k, h in enumerate(hosts):
+            ctx.get_fields(k, out=h)
+        n_e2e = max(3, min(args.steps, 10))
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            for k, h in enumerate(hosts):
+                ctx.set_fields(k, h)
+            _, st = ctx.iterate(1)
+            for k, h in enumerate(hosts):
+                ctx.get_fields(k, out=h)
+        e2e_s = _max_over_ranks(dist, time.perf_counter() - t0, f"cuda:{dev}")
+        nbytes = int(sum(h.nbytes for h in hosts))
+        res["e2e"] = {"value": ws * int(ncells.sum()) * n_e2e / e2e_s, "unit": METRIC,
+                      "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 48 * len(cases),
+                      "steps": n_e2e}
     ctx.destroy()
     return res
 
 
-def rooflines(res, mesh, precision):
+def fp64_peak(clocks):
+    """Derived FP64 peak in TFLOP/s: the FP64 units of the 152 SMs at the median SM clock
+    sampled during the timed region (the maximum clock if no sample was taken)."""
+    mhz = (clocks or {}).get("sm_mhz") or SM_MAX_MHZ
+    return SM_COUNT * FP64_FLOP_PER_SM_CLK * mhz * 1e6 / 1e12, mhz
+
+
+def rooflines(res, mesh, precision, workload, probe_tflops=None):
+    """The dominant kernel against the roofline that bounds it. The flux kernel is bound by
+    the FP64 pipe: achieved = algorithmic flops (FLUX_ALG_FLOPS_PER_FACE x faces) over its
+    CUDA-event time, against the derived FP64 peak at the sampled clock. The other kernels
+    against HBM: algorithmic bytes over time, against the measured copy bandwidth."""
     peaks, src = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     t = 4 if precision == "mixed" else 8
     km = res["kernel_ms"]
+    ncu = NCU.get(workload, {})
     dom = max(km, key=km.get)
     b = alg_bytes(dom, t, mesh.n_cells, mesh.n_faces)
     ach = b / (km[dom] / 1e3) / 1e9
-    per_cell = SWEEP_DRAM_BYTES_PER_CELL.get((dom, t))
+    per_cell = ncu.get("sweep_dram_bytes_per_cell", {}).get((dom, t))
     dominant = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": per_cell * mesh.n_cells if per_cell else None, "peak_source": f"hbm_gbs ({src}, burst copy)",
-                "alg_bytes_per_launch": b, "note": "latency-bound dependency chain: one block walks the "
-                "sweep's levels; the HBM fraction shows how far it is from any bandwidth limit"}
+                "traffic": per_cell * mesh.n_cells if per_cell else None,
+                "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({src}, burst copy)",
+                "alg_bytes_per_launch": b}
+    peak, mhz = fp64_peak(res.get("clocks"))
     flux_t = km["k_flux"]
-    ach_f = FLUX_FLOPS_PER_FACE * mesh.n_faces / (flux_t / 1e3) / 1e12
-    flux = {"bound": "alu", "kernel": "k_flux", "achieved": ach_f, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach_f / FP64_PEAK_TFLOPS,
-            "traffic": FLUX_DRAM_BYTES_PER_FACE * mesh.n_faces if FLUX_DRAM_BYTES_PER_FACE else None,
-            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
-            "flops_per_face": FLUX_FLOPS_PER_FACE}
-    if dom == "k_flux":
-        # the flux kernel is bound by the FP64 pipe, not by memory: report that roofline
+    ach_f = FLUX_ALG_FLOPS_PER_FACE * mesh.n_faces / (flux_t / 1e3) / 1e12
+    exe = ncu.get("flux_exec_flops_per_face")
+    dram = ncu.get("flux_dram_bytes_per_face")
+    flux = {"bound": "alu", "kernel": "k_flux", "achieved": ach_f, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach_f / peak, "traffic": dram * mesh.n_faces if dram else None,
+            "peak_source": f"derived: {SM_COUNT} SMs x 2 FP64 FMA/clk x 2 flop x {mhz:.0f} MHz (median SM clock "
+                           f"sampled during the timed region)",
+            "alg_flops_per_face": FLUX_ALG_FLOPS_PER_FACE, "faces_per_launch": mesh.n_faces,
+            "ms_per_launch": flux_t}
+    if probe_tflops:
+        flux.update(peak_measured_probe=probe_tflops, frac_of_probe=ach_f / probe_tflops)
+    if exe:
+        flux.update(executed_flops_per_face=exe, executed_tflops=exe * mesh.n_faces / (flux_t / 1e3) / 1e12,
+                    executed_source=ncu["source"])
+    if dominant["kernel"] == "k_flux":
         dominant = dict(flux, alg_bytes_per_launch=b, hbm_achieved_gbs=ach, hbm_frac=ach / hbm)
     return dominant, flux
 
@@ -348,6 +451,7 @@ def per_kernel(res, mesh, precision):
     also per dependency level (their bound is the depth of the sweep order)."""
     peaks, _ = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    peak, _ = fp64_peak(res.get("clocks"))
     t = 4 if precision == "mixed" else 8
     out = {}
     for k, ms in res["kernel_ms"].items():
@@ -356,8 +460,8 @@ def per_kernel(res, mesh, precision):
         if b:
             row.update(alg_bytes=b, gbs=b / (ms / 1e3) / 1e9, hbm_frac=b / (ms / 1e3) / 1e9 / hbm)
         if k == "k_flux":
-            tf = FLUX_FLOPS_PER_FACE * mesh.n_faces / (ms / 1e3) / 1e12
-            row.update(fp64_tflops=tf, fp64_frac=tf / FP64_PEAK_TFLOPS)
+            tf = FLUX_ALG_FLOPS_PER_FACE * mesh.n_faces / (ms / 1e3) / 1e12
+            row.update(fp64_tflops=tf, fp64_frac=tf / peak)
         lv = res.get("levels")
         if lv and k in ("k_sweep_fwd", "k_sweep_bwd"):
             n = lv[0] if k == "k_sweep_fwd" else lv[1]
@@ -372,9 +476,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="igks", choices=["igks", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
-                    help="headline sweep precision (the other one is measured too)")
-    ap.add_argument("--workload", default="turbulent_plate", choices=list(WORKLOADS) + ["naca_batch", "serving", "cavity"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
+                    help="headline sweep precision (default: mixed for the batch, fp64 for one solve)")
+    ap.add_argument("--workload", default="naca_batch", choices=list(WORKLOADS) + ["naca_batch", "serving", "cavity"])
     ap.add_argument("--explicit-cap", type=int, default=2000000, help="cavity: explicit iterations at most")
     ap.add_argument("--sweep-cluster", type=int, default=0,
                     help="blocks (thread-block cluster) per solve in the sweeps; 0: the library's choice")
@@ -391,11 +495,16 @@ def main():
                     help="cell numbering = LU-SGS sweep order (the oracle baseline runs the same)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-other", action="store_true", help="skip the other precision")
+    ap.add_argument("--no-other", action="store_true", help="skip the other precision / the flat plate")
+    ap.add_argument("--no-serving", action="store_true", help="batch: skip the bounded serving leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload == "naca_batch":
+        if args.impl == "reference":
+            return run_reference_batch(args)
         return main_batch(args)
+    if args.precision is None:
+        args.precision = "fp64"
     if args.workload == "serving":
         return main_serving(args)
     if args.workload == "cavity":
@@ -417,7 +526,7 @@ def main():
     head = measure(args, mesh, flow, args.precision, dev, dist, ws, with_e2e=True)
     other_p = "mixed" if args.precision == "fp64" else "fp64"
     other = None if args.no_other else measure(args, mesh, flow, other_p, dev, dist, ws, with_e2e=False)
-    dominant, flux_roof = rooflines(head, mesh, args.precision)
+    dominant, flux_roof = rooflines(head, mesh, args.precision, args.workload)
     out = {"metric": METRIC, "value": head["value"], "unit": METRIC, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
@@ -459,17 +568,80 @@ class _Totals:
         self.n_faces = sum(m.n_faces for m, _ in cases)
 
 
+def serving_leg(args, dev, n_small=11, budget_s=120.0):
+    """A bounded serving run beside the headline: the 64 x 32 laminar flat plate (whose
+    oracle solution to density residual 1e-10 is stored) plus n_small seeded requests of
+    the serving stream (2k-12k cells, SA, stop at residual 1e-10 or Eq. 40 <= 3e-8), all
+    submitted at once to one server (FP32 sweeps, continuous batching). Reports converged
+    solves/hour over the makespan, p50/p99 time to converged, and the plate's error
+    against the oracle's field."""
+    from paper_1709_00803_gb300 import igks
+    cases = [(G.laminar_plate(), F.laminar_plate_flow(), None)] + serving_cases(n_small, 2000, 12000, 3e-8)
+    srv = igks.Server(precision=igks.PREC_MIXED, max_slots=64, max_cohort=64, iters_per_step=args.iters_per_step,
+                      max_iters=args.max_iters, keep_fields=1)
+    t0 = srv.now()
+    ids = [srv.submit(m, fl, tag=k) for k, (m, fl, _) in enumerate(cases)]
+    results, wall0 = {}, time.perf_counter()
+    while len(results) < len(cases) and time.perf_counter() - wall0 < budget_s:
+        srv.step()
+        for r in srv.poll():
+            results[r["id"]] = r
+    timed_out = len(results) < len(cases)
+    lat = sorted(r["t_finish"] - r["t_submit"] for r in results.values() if r["state"] == igks.CONVERGED)
+    makespan = (max(r["t_finish"] for r in results.values()) - t0) if results else None
+    plate = results.get(ids[0])
+    err = None
+    gold = os.path.join(ROOT, "tests", "golden", "converged_laminar_plate.npz")
+    if plate and plate["state"] == igks.CONVERGED and os.path.exists(gold):
+        W = srv.take_fields(ids[0])
+        ref = np.load(gold)["W"]
+        err = float(np.max(np.linalg.norm(W[:4] - ref[:4], axis=1) / np.linalg.norm(ref[:4], axis=1)))
+    srv.destroy()
+    conv = len(lat)
+    return {"requests": len(cases), "finished": len(results), "converged": conv,
+            "solves_per_hour": conv / makespan * 3600.0 if makespan else None, "makespan_s": makespan,
+            "p50_s": _pct(lat, 50), "p99_s": _pct(lat, 99), "budget_s": budget_s, "hit_budget": timed_out,
+            "laminar_plate_rel_l2_vs_oracle": err,
+            "laminar_plate_iters": plate["iters"] if plate else None,
+            "stream": f"laminar flat plate 64x32 (residual 1e-10) + {n_small} seeded requests (flat plate or NACA "
+                      f"4-digit, SA, 2k-12k cells, residual 1e-10 or Eq. 40 <= 3e-8), all submitted at once, "
+                      f"FP32 sweeps, cap {args.max_iters} iterations"}
+
+
+def cpu_baseline_batch(cases, budget_s=15.0):
+    """The oracle as it stands, single-threaded, on a bounded sample of the batch: whole
+    iterations of its airfoils in order until budget_s has passed."""
+    import oracle as O
+    cells, used, dt = 0, 0, 0.0
+    for m, fl in cases:
+        ora = O.Oracle(m, fl)
+        t1 = time.perf_counter()
+        ora.iterate(1)
+        dt += time.perf_counter() - t1
+        cells += m.n_cells
+        used += 1
+        if dt >= budget_s:
+            break
+    return {"value": cells / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"one oracle iteration (from the free stream; set-up not timed) of each of the first {used} "
+                      f"airfoils of the batch ({cells} cell-updates), {dt:.1f} s, single-threaded C oracle "
+                      f"(-O2 -ffp-contract=off)"}
+
+
 def main_batch(args):
-    """Many uneven airfoil solves in one context, FP32 sweeps by default (--precision)."""
+    """The headline: many uneven airfoil solves in one context (FP32 sweeps by default),
+    with the turbulent flat plate and a bounded serving run beside it."""
     import torch
+    from paper_1709_00803_gb300 import igks
     dist, rank, ws = _dist()
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     cases = batch_cases(args.batch)
     tot = _Totals(cases)
-    precision = args.precision
-    head = measure_batch(args, cases, precision, dev, dist, ws)
-    dominant, flux_roof = rooflines(head, tot, precision)
+    precision = args.precision or "mixed"
+    probe = igks.fp64_probe(dev)
+    head = measure_batch(args, cases, precision, dev, dist, ws, with_e2e=True)
+    dominant, flux_roof = rooflines(head, tot, precision, "naca_batch", probe)
     desc = (f"{len(cases)} seeded NACA 4-digit airfoils (m 0-0.06, p 0.2-0.6, t 0.08-0.18), Ma 0.1-0.75, "
             f"AoA -4..8 deg, Re_c 1e6-1e7, SA, hybrid O-meshes of 8k-80k cells in one context")
     out = {"metric": METRIC, "value": head["value"], "unit": METRIC, "n_gpus": ws, "steps": args.steps,
@@ -477,13 +649,30 @@ def main_batch(args):
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if precision == "fp64" else "f64 flux/residual/update + f32 sweeps",
            "data": "synthetic",
-           "config": {"workload": desc, "cells": tot.n_cells, "faces": tot.n_faces, "precision": precision,
-                      "l2": "flushed between steps (256 MiB write outside the timed intervals)"},
-           "gpu_launches": head["launches_per_step"] * args.steps, "kernel_ms": head["kernel_ms"],
-           "roofline": dominant, "roofline_flux": flux_roof, "clocks": head["clocks"],
-           "per_kernel": per_kernel(head, tot, precision),
+           "config": {"workload": desc, "solves": len(cases), "cells": tot.n_cells, "faces": tot.n_faces,
+                      "precision": precision, "parallelism": "replicas" if ws > 1 else "one context, all solves",
+                      "l2": "not flushed: the state and mesh data of a step (over 2 GB) exceed the 129 MB L2",
+                      "timing": "one window of --steps iterations between CUDA events on the library stream"},
+           "e2e": head["e2e"], "gpu_launches": head["launches_per_step"] * args.steps,
+           "kernel_ms": head["kernel_ms"], "roofline": dominant, "roofline_flux": flux_roof,
+           "clocks": head["clocks"], "per_kernel": per_kernel(head, tot, precision),
            "batch": {k: head[k] for k in ("solves", "running", "converged", "diverged", "live_cells_first_last",
                                           "autotune")}}
+    if not args.no_other:
+        # the turbulent flat plate, one solve, both sweep precisions
+        mesh, flow = G.turbulent_plate(), F.turbulent_plate_flow()
+        plate = {}
+        for prec in ("fp64", "mixed"):
+            r = measure(args, mesh, flow, prec, dev, dist, ws, with_e2e=False)
+            plate[prec] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "kernel_ms": r["kernel_ms"],
+                           "sweep_levels": list(r["levels"]), "clocks": r["clocks"]}
+        out["turbulent_plate"] = dict(plate, workload=WORKLOADS["turbulent_plate"][2], cells=mesh.n_cells,
+                                      faces=mesh.n_faces)
+    if not args.no_serving and ws == 1:
+        out["serving"] = serving_leg(args, dev)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_batch(cases, args.cpu_budget)
+        out["cpu_baseline"]["cores_available"] = os.cpu_count()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:

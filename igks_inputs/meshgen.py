@@ -490,9 +490,9 @@ def triangle_fan(n: int = 4, radius: float = 1.0) -> Mesh:
 
 
 def mixed_polygons(seed: int = 0) -> Mesh:
-    """A small mesh mixing a quad row, a pentagon, a hexagon and triangles: the
-    general-polygon cells the hybrid meshes of the paper contain. Bottom is wall, the
-    right side outflow, the rest free stream."""
+    """A small mesh of eight cells: six quads, one pentagon and one triangle (general
+    polygons as in the paper's hybrid meshes). Bottom is wall, the right side outflow, the
+    rest free stream."""
     xy = np.array([
         [0.0, 0.0], [1.0, 0.0], [2.0, 0.0], [3.0, 0.0],      # 0..3 bottom
         [0.0, 1.0], [1.0, 1.0], [2.0, 1.0], [3.0, 1.0],      # 4..7
@@ -611,3 +611,70 @@ def cavity(n: int = 100) -> Mesh:
                    name=f"cavity_{n}x{n}")
     m.meta = dict(kind="cavity", n=n)
     return m
+
+
+def refined_cavity(n: int = 24, band: int = 3, patch=(0.5, 0.6, 0.16), jitter: float = 0.05,
+                   seed: int = 0, permute_seed=None) -> Mesh:
+    """Lid-driven cavity on an adaptively refined mesh of the kind the paper's second cavity
+    mesh is (quads, pentagons and hexagons): an n x n coarse grid on the unit square whose
+    cells within `band` cells of a wall, or with their centre inside the disc `patch`
+    (x, y, radius), are split into 2 x 2 quads. A coarse cell next to refined ones keeps
+    the refined side's middle node (a hanging node), so it becomes a pentagon (one refined
+    neighbour), a hexagon (two) or a polygon of up to eight nodes. Interior nodes are moved
+    by a seeded `jitter` x the fine spacing so that the polygons are not degenerate.
+    Cells are numbered by centroid (rows from the bottom), or by a seeded random
+    permutation (`permute_seed`), which gives cells with five or more lower or upper
+    neighbours in the LU-SGS sweep order. Walls as in `cavity`."""
+    rng = np.random.default_rng(seed)
+    m2 = 2 * n + 1
+    px, py, pr = patch
+    h = 1.0 / n
+    ref = np.zeros((n, n), dtype=bool)
+    for j in range(n):
+        for i in range(n):
+            near = min(i, j, n - 1 - i, n - 1 - j) < band
+            xc, yc = (i + 0.5) * h, (j + 0.5) * h
+            ref[j, i] = near or (xc - px) ** 2 + (yc - py) ** 2 <= pr * pr
+    lid = lambda I, J: J * m2 + I
+    cells = []
+    for j in range(n):
+        for i in range(n):
+            I, J = 2 * i, 2 * j
+            if ref[j, i]:
+                for b in range(2):
+                    for a in range(2):
+                        cells.append([lid(I + a, J + b), lid(I + a + 1, J + b), lid(I + a + 1, J + b + 1),
+                                      lid(I + a, J + b + 1)])
+                continue
+            refined = lambda ii, jj: 0 <= ii < n and 0 <= jj < n and ref[jj, ii]
+            poly = [lid(I, J)]
+            if refined(i, j - 1):
+                poly.append(lid(I + 1, J))
+            poly.append(lid(I + 2, J))
+            if refined(i + 1, j):
+                poly.append(lid(I + 2, J + 1))
+            poly.append(lid(I + 2, J + 2))
+            if refined(i, j + 1):
+                poly.append(lid(I + 1, J + 2))
+            poly.append(lid(I, J + 2))
+            if refined(i - 1, j):
+                poly.append(lid(I, J + 1))
+            cells.append(poly)
+    used = np.unique(np.concatenate([np.asarray(c) for c in cells]))
+    remap = -np.ones(m2 * m2, dtype=np.int64)
+    remap[used] = np.arange(used.shape[0])
+    I, J = used % m2, used // m2
+    xy = np.stack([I / (2.0 * n), J / (2.0 * n)], axis=1)
+    inner = (I > 0) & (I < 2 * n) & (J > 0) & (J < 2 * n)
+    xy[inner] += jitter * (0.5 * h) * rng.uniform(-1.0, 1.0, size=(int(inner.sum()), 2))
+    cells = [[int(remap[v]) for v in c] for c in cells]
+    cen = np.array([xy[c].mean(axis=0) for c in cells])
+    if permute_seed is None:
+        order = np.lexsort((cen[:, 0], np.round(cen[:, 1], 9)))
+    else:
+        order = np.random.default_rng(permute_seed).permutation(len(cells))
+    cells = [cells[k] for k in order]
+    mesh = build_mesh(xy, cells, lambda a, b, xm, ym: BC_MOVING_WALL if abs(ym - 1.0) < 1e-12 else BC_WALL,
+                      name=f"refined_cavity_{n}")
+    mesh.meta = dict(kind="refined_cavity", n=n)
+    return mesh

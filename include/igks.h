@@ -78,7 +78,11 @@ typedef struct igks_options {
   int32_t sweep_cluster;  /* schedule 1: a thread-block cluster of 1 (0: 1), 2, 4 or 8 blocks per
                              solve shares each level (distributed shared memory, one cluster
                              barrier per level); same arithmetic, same bits */
-  int32_t reserved[4];
+  int32_t groups;         /* schedule 1 with several solves: split them into this many groups of
+                             consecutive solves (0: 1), each iterated by a graph on a stream of
+                             its own, so that one group's sweeps (one block per solve) overlap
+                             another group's flux; same arithmetic, same bits */
+  int32_t reserved[3];
 } igks_options;
 
 /* Flow conditions of one solve. Non-dimensional: free-stream density, speed and the
@@ -201,6 +205,12 @@ int igks_set_scalars(igks_ctx* ctx, int32_t solve, const double* in /*[5]*/);
 #define IGKS_ARR_GEOM_FACE 11
 int igks_get_array(igks_ctx* ctx, int32_t solve, int32_t which, double* out);
 
+/* Residual history of a solve (Eq. 25's norms, iteration by iteration; kept on the device
+ * for the last 1024 iterations): out[3k] the iteration (1-based), out[3k+1] the RMS over
+ * cells of M_rho / Omega, out[3k+2] max |M_rho|, oldest first, for the last min(iterations
+ * done, 1024, cap) iterations; *n receives the count. */
+int igks_get_history(igks_ctx* ctx, int32_t solve, int32_t cap, double* out /*[3*cap]*/, int32_t* n);
+
 /* Sizes of a solve: out[0] n_cells, out[1] n_faces, out[2] forward sweep levels,
  * out[3] backward sweep levels, out[4] boundary faces. */
 int igks_mesh_info(igks_ctx* ctx, int32_t solve, int32_t* out /*[5]*/);
@@ -216,15 +226,21 @@ typedef struct igks_tuning {
   int32_t sweep_mode;      /* 1 one block per solve, 2 one launch per level */
   int32_t sweep_cluster;   /* blocks per solve of schedule 1 */
   float ms_per_iter;       /* measured device time of one iteration with it */
+  int32_t groups;          /* groups of solves on streams of their own (igks_options.groups) */
 } igks_tuning;
 
 /* Time the library's launch configurations (sweep schedule, block size and blocks per
- * solve, flux block size) on the context's live solves, iters_per_trial iterations each after one warm-up
+ * solve, flux block size, groups of solves) on the context's live solves, iters_per_trial iterations each after one warm-up
  * iteration, and keep the fastest. Every trial starts from the same saved state and the
  * state is restored afterwards: the configurations do not change the arithmetic, so the
  * solves' iterates are exactly those of an untuned run. Allocates temporary device
  * memory. out (nullable) receives the choice. Errors: IGKS_EINVAL, IGKS_ECUDA. */
 int igks_autotune(igks_ctx* ctx, int32_t iters_per_trial, igks_tuning* out);
+
+/* Apply a launch configuration (as igks_autotune returns it; ms_per_iter is ignored) without
+ * timing anything: the solves' iterates do not depend on it. Errors: IGKS_EINVAL (a value
+ * outside the choices igks_autotune tries), IGKS_ECUDA. */
+int igks_set_launch(igks_ctx* ctx, const igks_tuning* t);
 
 /* Number of kernel launches one iteration issues (for launch accounting). */
 int igks_launches_per_iteration(igks_ctx* ctx, int32_t* out);
@@ -249,10 +265,10 @@ int igks_destroy(igks_ctx* ctx);
  * memory -- code running while the stream is being captured into a CUDA graph, hosts
  * whose GPU memory comes only from their own pool or arena, real-time loops that cannot
  * afford an allocation's latency or failure).
- *   m_rho  DEVICE pointer, [n_cells] density residual M_rho of Eq. 16, one per cell
- *   area   DEVICE pointer, [n_cells] cell areas Omega
- *   out    DEVICE pointer, [2]: out[0] = max |M_rho| (the norm of Eq. 25),
- *                               out[1] = RMS over cells of M_rho / Omega
+ *   m_rho  DEVICE pointer, [n_cells] per-cell density residual (IGKS_ARR_RES component 0)
+ *   area   DEVICE pointer, [n_cells] cell areas
+ *   out    DEVICE pointer, [2]: out[0] = max |m_rho| over the cells,
+ *                               out[1] = RMS over cells of m_rho / area
  *   stream cudaStream_t the two kernels run on (NULL: the legacy default stream)
  * It computes the same reduction, in the same order, as igks_iterate does for its
  * status. Inputs and outputs belong to the caller; the only other memory used is a
@@ -263,11 +279,19 @@ int igks_destroy(igks_ctx* ctx);
  * Every call shares the scratch array and it keeps the last call's contents; each call
  * writes all it reads, but calls whose kernels overlap on the GPU race on it.
  * Asynchronous: returns after enqueueing; out is valid once the stream reaches it.
- * Errors: IGKS_EINVAL for null pointers, n_cells <= 0 or n_cells > IGKS_NOALLOC_MAX_CELLS
- * (message in igks_last_error(NULL)), IGKS_ECUDA for a CUDA error. */
+ * Errors: IGKS_EINVAL for null pointers, n_cells <= 0, n_cells > IGKS_NOALLOC_MAX_CELLS or
+ * a current device ordinal of 64 or more (message in igks_last_error(NULL)), IGKS_ECUDA for
+ * a CUDA error. */
 #define IGKS_NOALLOC_MAX_CELLS (1 << 20)
 int igks_residual_norms_noalloc(const double* m_rho, const double* area, int32_t n_cells,
                                 double* out, void* stream);
+
+/* Measured FP64 arithmetic rate of a device, for the roofline of the FP64-bound flux
+ * kernel (measurement support; no counterpart in the paper): eight independent chains of
+ * fused multiply-adds per thread over eight 256-thread blocks per SM, best of three timed
+ * launches after a warm-up, in TFLOP/s (an FMA counts two flops). Takes about 30 ms.
+ * Errors: IGKS_EINVAL (null tflops), IGKS_ECUDA. */
+int igks_fp64_probe(int32_t device, double* tflops);
 
 /* Message of the last error on this context (owned by the context; never NULL). */
 const char* igks_last_error(igks_ctx* ctx);
@@ -329,6 +353,8 @@ typedef struct igks_request {
   const int32_t* face_bc;
   igks_flow flow;
   int64_t tag;              /* caller's value, returned in the result */
+  const double* W0;         /* nullable: starting state [5*n_cells] SoA as for igks_set_fields
+                               (a warm start, copied at submit); NULL starts from the free stream */
 } igks_request;
 
 typedef struct igks_result {
@@ -360,8 +386,10 @@ typedef struct igks_server igks_server;
 /* Errors: IGKS_EINVAL (bad option), IGKS_ECUDA. */
 int igks_server_create(const igks_server_options* opt, igks_server** out);
 /* Queue one request; *id receives its id (ids count up from 0). The mesh is validated
- * here (IGKS_EMESH) and the flow too (IGKS_EINVAL). A request whose footprint exceeds
- * the whole budget is refused with IGKS_ENOMEM. */
+ * here (IGKS_EMESH), the flow and a given W0 too (IGKS_EINVAL: non-positive density or
+ * non-finite energy, as igks_set_fields). A request whose footprint exceeds the whole
+ * budget is refused with IGKS_ENOMEM. A solve that diverges (non-positive density or
+ * pressure, or a non-finite state, during an update) finishes with IGKS_DIVERGED. */
 int igks_server_submit(igks_server* srv, const igks_request* req, int64_t* id);
 /* One retire/admit/run round as described above. status (nullable) describes the
  * server after the step. Errors: IGKS_ECUDA, IGKS_ENOMEM (a cohort could not be

@@ -47,15 +47,22 @@ struct igks_ctx {
   std::vector<Buf> bufs;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
   std::string err = "";
   // layout
   std::vector<int> cell_off, cell_pad, face_off, node_off;
   SolveState* h_st = nullptr;   // pinned mirror of the per-solve state
   int nc_pad = 0, nf = 0, nn = 0;
-  cudaEvent_t ev[N_KERNEL_KINDS + 1] = {};
   std::vector<int> h_wfwd_ptr, h_wbwd_ptr;   // wide schedule level offsets (host copies)
+  // groups of consecutive solves, each iterated on a stream of its own (one group: the
+  // context stream); per group its launch ranges, stream, graph and timing events
+  int n_groups = 1;
+  std::vector<Dev> gdev;
+  std::vector<cudaStream_t> gstream;
+  std::vector<cudaGraph_t> ggraph;
+  std::vector<cudaGraphExec_t> ggexec;
+  std::vector<std::vector<cudaEvent_t>> gev;
+  std::vector<cudaEvent_t> join_ev;
+  cudaEvent_t fork_ev = nullptr;
 };
 
 static int fail(igks_ctx* c, int code, const std::string& msg) {
@@ -141,11 +148,30 @@ static int upload(igks_ctx* ctx, const T** out, const std::vector<T>& h) {
   return 0;
 }
 
+// the per-group streams, graphs and events (group 0's stream is the context stream when
+// there is one group)
+static void release_groups(igks_ctx* ctx) {
+  for (auto& g : ctx->ggexec) if (g) cudaGraphExecDestroy(g);
+  for (auto& g : ctx->ggraph) if (g) cudaGraphDestroy(g);
+  ctx->ggexec.clear();
+  ctx->ggraph.clear();
+  for (auto& evs : ctx->gev)
+    for (auto e : evs) if (e) cudaEventDestroy(e);
+  ctx->gev.clear();
+  for (auto e : ctx->join_ev) if (e) cudaEventDestroy(e);
+  ctx->join_ev.clear();
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  ctx->fork_ev = nullptr;
+  for (auto st : ctx->gstream)
+    if (st && st != ctx->stream) cudaStreamDestroy(st);
+  ctx->gstream.clear();
+  ctx->gdev.clear();
+}
+
 static void release(igks_ctx* ctx) {
-  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
-  if (ctx->graph) cudaGraphDestroy(ctx->graph);
-  ctx->gexec = nullptr;
-  ctx->graph = nullptr;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto st : ctx->gstream) if (st) cudaStreamSynchronize(st);
+  release_groups(ctx);
   for (auto& b : ctx->bufs) cudaFree(b.p);
   ctx->bufs.clear();
   if (ctx->h_st) cudaFreeHost(ctx->h_st);
@@ -157,26 +183,116 @@ static const char* const KERNEL_NAMES[N_KERNEL_KINDS] = {
     "k_prep", "k_ghost", "k_gradient", "k_flux", "k_residual", "k_norms",
     "k_sweep_prep", "k_sweep_fwd", "k_sweep_bwd", "k_update", "k_end_iter"};
 
-// issue one iteration's kernels on the context stream (with an event after each kernel
+// issue one iteration's kernels of group g on its stream (with an event after each kernel
 // when timing is on; event k+1 minus event k is the duration of kernel k)
-static void enqueue_iteration(igks_ctx* ctx) {
-  const Dev& d = ctx->dev;
-  cudaStream_t s = ctx->stream;
+static void enqueue_iteration(igks_ctx* ctx, int g) {
+  const Dev& d = ctx->gdev[g];
+  cudaStream_t s = ctx->gstream[g];
   const int p = ctx->opt.precision, th = ctx->opt.sweep_threads;
   const bool t = ctx->opt.timing != 0;
+  cudaEvent_t* ev = t ? ctx->gev[g].data() : nullptr;
   int e = 0;
-  if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
-  launch_prep(d, s);                   if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
-  launch_ghost(d, s);                  if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
-  launch_gradient(d, s);               if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
-  launch_flux(d, s);                   if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
-  launch_residual(d, s);               if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
-  launch_norms(d, s);                  if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
-  launch_sweep_prep(d, p, s);          if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
-  launch_sweep_fwd(d, p, th, s);       if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
-  launch_sweep_bwd(d, p, th, s);       if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
-  launch_update(d, p, s);              if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
-  launch_end_iter(d, s);               if (t) cudaEventRecordWithFlags(ctx->ev[e++], s, cudaEventRecordExternal);
+  if (t) cudaEventRecordWithFlags(ev[e++], s, cudaEventRecordExternal);
+  launch_prep(d, s);                   if (t) cudaEventRecordWithFlags(ev[e++], s, cudaEventRecordExternal);
+  launch_ghost(d, s);                  if (t) cudaEventRecordWithFlags(ev[e++], s, cudaEventRecordExternal);
+  launch_gradient(d, s);               if (t) cudaEventRecordWithFlags(ev[e++], s, cudaEventRecordExternal);
+  launch_flux(d, s);                   if (t) cudaEventRecordWithFlags(ev[e++], s, cudaEventRecordExternal);
+  launch_residual(d, s);               if (t) cudaEventRecordWithFlags(ev[e++], s, cudaEventRecordExternal);
+  launch_norms(d, s);                  if (t) cudaEventRecordWithFlags(ev[e++], s, cudaEventRecordExternal);
+  launch_sweep_prep(d, p, s);          if (t) cudaEventRecordWithFlags(ev[e++], s, cudaEventRecordExternal);
+  launch_sweep_fwd(d, p, th, s);       if (t) cudaEventRecordWithFlags(ev[e++], s, cudaEventRecordExternal);
+  launch_sweep_bwd(d, p, th, s);       if (t) cudaEventRecordWithFlags(ev[e++], s, cudaEventRecordExternal);
+  launch_update(d, p, s);              if (t) cudaEventRecordWithFlags(ev[e++], s, cudaEventRecordExternal);
+  launch_end_iter(d, s);               if (t) cudaEventRecordWithFlags(ev[e++], s, cudaEventRecordExternal);
+}
+
+// the whole context as one launch range
+static void whole_range(Dev& d) {
+  d.g_blk0 = 0; d.g_nblk = d.n_cell_blocks;
+  d.g_face0 = 0; d.g_nface = d.nf;
+  d.g_solve0 = 0; d.g_nsolve = d.n_solves;
+}
+
+// Split the solves into groups of consecutive solves with about equal cell counts (one
+// group with the wide schedule, whose per-level launches span all solves), give each its
+// launch ranges, a stream and timing events, and capture one iteration of each as a graph.
+static int setup_groups(igks_ctx* ctx) {
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto st : ctx->gstream) if (st) cudaStreamSynchronize(st);
+  release_groups(ctx);
+  Dev& d = ctx->dev;
+  whole_range(d);
+  const int ns = d.n_solves;
+  int G = std::max(1, std::min(ctx->opt.groups, ns));
+  if (d.wide) G = 1;
+  ctx->n_groups = G;
+  std::vector<int> cut(1, 0);
+  {
+    int64_t total = 0, acc = 0;
+    for (int s = 0; s < ns; s++) total += ctx->cell_pad[s];
+    for (int s = 0; s < ns && (int)cut.size() < G; s++) {
+      acc += ctx->cell_pad[s];
+      if (acc * G >= total * (int64_t)cut.size() && ns - (s + 1) >= G - (int)cut.size()) cut.push_back(s + 1);
+    }
+    while ((int)cut.size() < G) cut.push_back(cut.back() + 1);
+    cut.push_back(ns);
+  }
+  for (int g = 0; g < G; g++) {
+    Dev v = d;
+    const int s0 = cut[g], s1 = cut[g + 1];
+    v.g_solve0 = s0; v.g_nsolve = s1 - s0;
+    v.g_blk0 = ctx->cell_off[s0] / CELL_BLOCK;
+    v.g_nblk = (s1 < ns ? ctx->cell_off[s1] : ctx->nc_pad) / CELL_BLOCK - v.g_blk0;
+    v.g_face0 = ctx->face_off[s0];
+    v.g_nface = (s1 < ns ? ctx->face_off[s1] : ctx->nf) - v.g_face0;
+    ctx->gdev.push_back(v);
+    cudaStream_t st = ctx->stream;
+    if (G > 1) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    ctx->gstream.push_back(st);
+    std::vector<cudaEvent_t> evs(N_KERNEL_KINDS + 1, nullptr);
+    if (ctx->opt.timing)
+      for (auto& e : evs) CK(cudaEventCreate(&e));
+    ctx->gev.push_back(evs);
+    cudaEvent_t j = nullptr;
+    if (G > 1) CK(cudaEventCreateWithFlags(&j, cudaEventDisableTiming));
+    ctx->join_ev.push_back(j);
+  }
+  if (G > 1) CK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+  ctx->ggraph.assign(G, nullptr);
+  ctx->ggexec.assign(G, nullptr);
+  if (ctx->opt.use_graph) {
+    for (int g = 0; g < G; g++) {
+      CK(cudaStreamBeginCapture(ctx->gstream[g], cudaStreamCaptureModeThreadLocal));
+      enqueue_iteration(ctx, g);
+      cudaError_t e = cudaStreamEndCapture(ctx->gstream[g], &ctx->ggraph[g]);
+      if (e != cudaSuccess) return fail(ctx, IGKS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      CK(cudaGraphInstantiate(&ctx->ggexec[g], ctx->ggraph[g], 0));
+    }
+  }
+  return 0;
+}
+
+// n iterations of every group, stream-ordered after the work already on the context stream
+// and before whatever the caller puts on it next
+static int run_iterations(igks_ctx* ctx, int n) {
+  const int G = ctx->n_groups;
+  if (G > 1) {
+    CK(cudaEventRecord(ctx->fork_ev, ctx->stream));
+    for (int g = 0; g < G; g++) CK(cudaStreamWaitEvent(ctx->gstream[g], ctx->fork_ev, 0));
+  }
+  for (int r = 0; r < n; r++)
+    for (int g = 0; g < G; g++) {
+      if (ctx->ggexec[g]) CK(cudaGraphLaunch(ctx->ggexec[g], ctx->gstream[g]));
+      else enqueue_iteration(ctx, g);
+    }
+  if (G > 1) {
+    for (int g = 0; g < G; g++) {
+      CK(cudaEventRecord(ctx->join_ev[g], ctx->gstream[g]));
+      CK(cudaStreamWaitEvent(ctx->stream, ctx->join_ev[g], 0));
+    }
+  }
+  CK(cudaGetLastError());
+  return 0;
 }
 
 // dependency levels of the sequential sweep: forward uses lower neighbours, backward upper
@@ -384,6 +500,7 @@ static int build(igks_ctx* ctx) {
   d = Dev{};
   d.n_solves = ns; d.nc_pad = nc; d.nf = nf; d.nn = nn; d.nbf = (int)bface.size();
   d.n_cell_blocks = nc / CELL_BLOCK;
+  whole_range(d);
   int rc = 0;
 #define UP(field, vec) if ((rc = upload(ctx, &d.field, vec))) { release(ctx); return rc; }
 #define AL(field, type, n) if ((rc = dalloc(ctx, (type**)&d.field, n))) { release(ctx); return rc; }
@@ -396,14 +513,16 @@ static int build(igks_ctx* ctx) {
   AL(area, double, nc); AL(cx, double, nc); AL(cy, double, nc); AL(wall_d, double, nc);
   AL(W, double, 5 * (size_t)nc); AL(grad, double, 8 * (size_t)nc); AL(phi, double, 4 * (size_t)nc);
   AL(omega, double, nc); AL(mu_l, double, nc); AL(mu_t, double, nc); AL(Lam, double, nc);
+  AL(pu, double, nc); AL(pv, double, nc); AL(pc, double, nc);
   AL(M, double, 5 * (size_t)nc); AL(fw, double, nc); AL(sa_diag, double, nc);
   AL(dWs, double, 5 * (size_t)nc); AL(dW, double, 5 * (size_t)nc); AL(dF, double, 8 * (size_t)nc);
   AL(fS, double, nf); AL(fnx, double, nf); AL(fny, double, nf); AL(fmx, double, nf); AL(fmy, double, nf);
-  AL(fcx, double, nf); AL(fcy, double, nf); AL(fdL, double, nf); AL(fdR, double, nf); AL(fdn, double, nf);
+  AL(fcx, double, nf); AL(fcy, double, nf); AL(fidL, double, nf); AL(fidR, double, nf); AL(fdn, double, nf);
   AL(lam_f, double, nf); AL(F, double, 6 * (size_t)nf); AL(sa_a, double, 4 * (size_t)nf);
   AL(G, double, 5 * (size_t)nf); AL(Gmu, double, 2 * (size_t)nf);
   AL(st, SolveState, ns); AL(dt_bits, unsigned long long, ns);
   AL(part, double, 2 * (size_t)d.n_cell_blocks); AL(err, int, 4);
+  AL(hist, double, 2 * (size_t)HIST * ns);
   AL(eq40_bits, unsigned long long, ns); AL(bad, int, ns);
   d.nnz = (int)cf_face.size();
   AL(sw_cell, double, 5 * (size_t)nc); AL(sw_st, double, 4 * (size_t)d.nnz); AL(sw_j, int, d.nnz);
@@ -485,14 +604,9 @@ static int build(igks_ctx* ctx) {
   for (int s = 0; s < ns; s++) ctx->dev.n_solves = ns;
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->built = true;
-  // ---- capture one iteration ----
-  if (ctx->opt.use_graph) {
-    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_iteration(ctx);
-    cudaError_t e = cudaStreamEndCapture(ctx->stream, &ctx->graph);
-    if (e != cudaSuccess) { release(ctx); return fail(ctx, IGKS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e)); }
-    CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
-  }
+  // ---- groups of solves, one iteration of each captured as a graph ----
+  rc = setup_groups(ctx);
+  if (rc) { release(ctx); return rc; }
   return 0;
 }
 
@@ -512,6 +626,7 @@ int igks_create(const igks_options* opt, igks_ctx** out) {
   if (ctx->opt.sweep_threads > NARROW_THREADS || ctx->opt.sweep_threads % 32) { delete ctx; return IGKS_EINVAL; }
   if (ctx->opt.precision != IGKS_PREC_FP64 && ctx->opt.precision != IGKS_PREC_MIXED) { delete ctx; return IGKS_EINVAL; }
   if (ctx->opt.sweep_cluster <= 0) ctx->opt.sweep_cluster = 1;
+  if (ctx->opt.groups <= 0) ctx->opt.groups = 1;
   if (ctx->opt.sweep_cluster != 1 && ctx->opt.sweep_cluster != 2 && ctx->opt.sweep_cluster != 4 &&
       ctx->opt.sweep_cluster != 8) { delete ctx; return IGKS_EINVAL; }
   cudaError_t e = cudaSetDevice(ctx->opt.device);
@@ -523,9 +638,6 @@ int igks_create(const igks_options* opt, igks_ctx** out) {
     if (e != cudaSuccess) { delete ctx; return IGKS_ECUDA; }
     ctx->own_stream = true;
   }
-  if (ctx->opt.timing)
-    for (auto& ev : ctx->ev)
-      if (cudaEventCreate(&ev) != cudaSuccess) { igks_destroy(ctx); return IGKS_ECUDA; }
   *out = ctx;
   return IGKS_OK;
 }
@@ -534,22 +646,22 @@ int igks_enqueue(igks_ctx* ctx, int32_t n_iters) {
   if (!ctx || n_iters < 0) return IGKS_EINVAL;
   int rc = build(ctx);
   if (rc) return rc;
-  for (int r = 0; r < n_iters; r++) {
-    if (ctx->gexec) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
-    else enqueue_iteration(ctx);
-  }
-  CK(cudaGetLastError());
-  return IGKS_OK;
+  return run_iterations(ctx, n_iters);
 }
 
 int igks_kernel_times(igks_ctx* ctx, int32_t cap, float* ms, int32_t* n) {
   if (!ctx || !ms || !n || cap < 0) return IGKS_EINVAL;
   if (!ctx->opt.timing) return fail(ctx, IGKS_EBUSY, "context created without timing");
+  if (!ctx->built) return fail(ctx, IGKS_EBUSY, "no iteration has run yet");
   *n = N_KERNEL_KINDS;
   for (int k = 0; k < N_KERNEL_KINDS && k < cap; k++) {
-    float t = 0.0f;
-    CK(cudaEventElapsedTime(&t, ctx->ev[k], ctx->ev[k + 1]));
-    ms[k] = t;
+    float sum = 0.0f;
+    for (int g = 0; g < ctx->n_groups; g++) {
+      float t = 0.0f;
+      CK(cudaEventElapsedTime(&t, ctx->gev[g][k], ctx->gev[g][k + 1]));
+      sum += t;
+    }
+    ms[k] = sum;
   }
   return IGKS_OK;
 }
@@ -685,11 +797,8 @@ int igks_iterate(igks_ctx* ctx, int32_t max_iters, igks_status* status) {
   bool any_live = true;
   while (done < max_iters && any_live) {
     int k = std::min(ctx->opt.check_every, max_iters - done);
-    for (int r = 0; r < k; r++) {
-      if (ctx->gexec) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
-      else enqueue_iteration(ctx);
-    }
-    CK(cudaGetLastError());
+    rc = run_iterations(ctx, k);
+    if (rc) return rc;
     done += k;
     CK(cudaMemcpyAsync(ctx->h_st, ctx->dev.st, sizeof(SolveState) * ns, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -827,6 +936,26 @@ int igks_get_array(igks_ctx* ctx, int32_t solve, int32_t which, double* out) {
   return fail(ctx, IGKS_EINVAL, "unknown array id");
 }
 
+int igks_get_history(igks_ctx* ctx, int32_t solve, int32_t cap, double* out, int32_t* n) {
+  if (check_solve(ctx, solve) || !n || cap < 0 || (cap > 0 && !out)) return IGKS_EINVAL;
+  int rc = build(ctx);
+  if (rc) return rc;
+  SolveState q;
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(d2h(ctx, &q, ctx->dev.st + solve, sizeof q));
+  std::vector<double> h(2 * (size_t)HIST);
+  CK(d2h(ctx, h.data(), ctx->dev.hist + (size_t)solve * HIST * 2, sizeof(double) * h.size()));
+  const int m = std::min({q.iter, HIST, (int)cap});
+  for (int k = 0; k < m; k++) {
+    const int it = q.iter - m + k;            // 0-based iteration index
+    out[3 * k] = it + 1;
+    out[3 * k + 1] = h[2 * (it % HIST)];
+    out[3 * k + 2] = h[2 * (it % HIST) + 1];
+  }
+  *n = m;
+  return IGKS_OK;
+}
+
 int igks_mesh_info(igks_ctx* ctx, int32_t solve, int32_t* out) {
   if (check_solve(ctx, solve) || !out) return IGKS_EINVAL;
   int rc = build(ctx);
@@ -915,17 +1044,8 @@ int igks_order_cells(int32_t n_cells, int32_t n_faces, const int32_t* face_cells
   return IGKS_OK;
 }
 
-// re-capture the iteration graph after a launch parameter changed
-static int recapture(igks_ctx* ctx) {
-  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
-  if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
-  if (!ctx->opt.use_graph) return 0;
-  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-  enqueue_iteration(ctx);
-  CK(cudaStreamEndCapture(ctx->stream, &ctx->graph));
-  CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
-  return 0;
-}
+// re-capture the iteration graphs after a launch parameter changed
+static int recapture(igks_ctx* ctx) { return setup_groups(ctx); }
 
 int igks_autotune(igks_ctx* ctx, int32_t iters_per_trial, igks_tuning* out) {
   if (!ctx || iters_per_trial <= 0) return IGKS_EINVAL;
@@ -963,30 +1083,32 @@ int igks_autotune(igks_ctx* ctx, int32_t iters_per_trial, igks_tuning* out) {
   const int flux_blocks[] = {64, 128};
   const int sweep_threads[] = {128, 256};
   const int clusters[] = {1, 2, 4};
+  const int groups[] = {1, 2, 4};
   int err = 0;
   for (int wide = 0; wide <= (wide_ok ? 1 : 0) && !err; wide++)
     for (int fb : flux_blocks)
       for (int stt : sweep_threads)
-        for (int cl : clusters) {
-        if (wide && (stt != sweep_threads[0] || cl != 1)) continue;   // the wide schedule has its own block
-        d.wide = wide;
-        d.flux_block = fb;
-        d.sweep_cluster = cl;
-        ctx->opt.sweep_threads = stt;
-        if ((err = recapture(ctx))) break;
-        restore();
-        for (int r = 0; r <= iters_per_trial; r++) {
-          if (r == 1) cudaEventRecord(e0, ctx->stream);   // the first iteration warms up
-          if (ctx->gexec) cudaGraphLaunch(ctx->gexec, ctx->stream);
-          else enqueue_iteration(ctx);
-        }
-        cudaEventRecord(e1, ctx->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) { err = IGKS_ECUDA; break; }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= iters_per_trial;
-        if (ms < best.ms_per_iter) best = igks_tuning{stt, fb, wide ? 2 : 1, cl, ms};
-        }
+        for (int cl : clusters)
+          for (int gr : groups) {
+          if (wide && (stt != sweep_threads[0] || cl != 1 || gr != 1)) continue;   // the wide schedule has its own block
+          if (gr > 1 && (cl != 1 || gr > ns)) continue;
+          d.wide = wide;
+          d.flux_block = fb;
+          d.sweep_cluster = cl;
+          ctx->opt.sweep_threads = stt;
+          ctx->opt.groups = gr;
+          if ((err = recapture(ctx))) break;
+          restore();
+          if ((err = run_iterations(ctx, 1))) break;     // the first iteration warms up
+          cudaEventRecord(e0, ctx->stream);
+          if ((err = run_iterations(ctx, iters_per_trial))) break;
+          cudaEventRecord(e1, ctx->stream);
+          if (cudaEventSynchronize(e1) != cudaSuccess) { err = IGKS_ECUDA; break; }
+          float ms = 0.0f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          ms /= iters_per_trial;
+          if (ms < best.ms_per_iter) best = igks_tuning{stt, fb, wide ? 2 : 1, cl, ms, gr};
+          }
   // apply the winner and put every solve back where it was
   d.wide = best.sweep_mode == 2;
   d.flux_block = best.flux_block;
@@ -994,6 +1116,7 @@ int igks_autotune(igks_ctx* ctx, int32_t iters_per_trial, igks_tuning* out) {
   ctx->opt.sweep_threads = best.sweep_threads;
   ctx->opt.sweep_mode = best.sweep_mode;
   ctx->opt.sweep_cluster = best.sweep_cluster;
+  ctx->opt.groups = best.groups;
   if (!err) err = recapture(ctx);
   restore();
   cudaStreamSynchronize(ctx->stream);
@@ -1008,11 +1131,31 @@ int igks_autotune(igks_ctx* ctx, int32_t iters_per_trial, igks_tuning* out) {
   return IGKS_OK;
 }
 
+int igks_set_launch(igks_ctx* ctx, const igks_tuning* t) {
+  if (!ctx || !t) return IGKS_EINVAL;
+  if ((t->sweep_threads != 128 && t->sweep_threads != 256) || (t->flux_block != 64 && t->flux_block != 128) ||
+      (t->sweep_mode != 1 && t->sweep_mode != 2) ||
+      (t->sweep_cluster != 1 && t->sweep_cluster != 2 && t->sweep_cluster != 4 && t->sweep_cluster != 8) ||
+      t->groups < 1)
+    return fail(ctx, IGKS_EINVAL, "launch configuration outside the tuner's choices");
+  int rc = build(ctx);
+  if (rc) return rc;
+  Dev& d = ctx->dev;
+  d.wide = t->sweep_mode == 2;
+  d.flux_block = t->flux_block;
+  d.sweep_cluster = t->sweep_cluster;
+  ctx->opt.sweep_threads = t->sweep_threads;
+  ctx->opt.sweep_mode = t->sweep_mode;
+  ctx->opt.sweep_cluster = t->sweep_cluster;
+  ctx->opt.groups = t->groups;
+  return recapture(ctx);
+}
+
 int igks_launches_per_iteration(igks_ctx* ctx, int32_t* out) {
   if (!ctx || !out) return IGKS_EINVAL;
   int rc = build(ctx);
   if (rc) return rc;
-  *out = N_KERNEL_KINDS - 2 + (ctx->dev.wide ? ctx->dev.n_wfwd + ctx->dev.n_wbwd : 2);
+  *out = ctx->n_groups * (N_KERNEL_KINDS - 2 + (ctx->dev.wide ? ctx->dev.n_wfwd + ctx->dev.n_wbwd : 2));
   return IGKS_OK;
 }
 
@@ -1020,8 +1163,6 @@ int igks_destroy(igks_ctx* ctx) {
   if (!ctx) return IGKS_EINVAL;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   release(ctx);
-  for (auto& ev : ctx->ev)
-    if (ev) cudaEventDestroy(ev);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return IGKS_OK;
@@ -1030,11 +1171,12 @@ int igks_destroy(igks_ctx* ctx) {
 int igks_footprint_bytes(int32_t n_nodes, int32_t n_cells, int32_t n_faces, int32_t nnz, int64_t* out) {
   if (n_nodes <= 0 || n_cells <= 0 || n_faces <= 0 || nnz < 0 || !out) return IGKS_EINVAL;
   const int64_t ncp = (int64_t)(n_cells + CELL_ALIGN - 1) / CELL_ALIGN * CELL_ALIGN;
-  // per padded cell: 115 doubles (state, gradients, increments, sweep records) + 32 ints
-  // (CSR pointers, orders, levels, positions, padded stencils); per CSR entry 60 B (face
-  // and node lists, sweep stencil coefficients, maps) + 40 B (one sweep entry); per face
-  // 34 doubles + 8 ints; per node 2 doubles; a few hundred bytes per solve
-  *out = 1048 * ncp + 100 * (int64_t)nnz + 304 * (int64_t)n_faces + 16 * (int64_t)n_nodes + 4096;
+  // (plus 16 KiB of residual history per solve, in the fixed part below)
+  // per padded cell: 118 doubles (state, gradients, speeds, increments, sweep records) +
+  // 32 ints (CSR pointers, orders, levels, positions, padded stencils); per CSR entry 60 B
+  // (face and node lists, sweep stencil coefficients, maps) + 40 B (one sweep entry); per
+  // face 34 doubles + 8 ints; per node 2 doubles; a few hundred bytes per solve
+  *out = 1072 * ncp + 100 * (int64_t)nnz + 304 * (int64_t)n_faces + 16 * (int64_t)n_nodes + 4096 + 16384;
   return IGKS_OK;
 }
 

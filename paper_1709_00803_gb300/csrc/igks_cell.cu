@@ -68,7 +68,7 @@ __global__ void k_geometry_faces(Dev d) {
     dR = dL;
   }
   d.fS[f] = S; d.fnx[f] = nx; d.fny[f] = ny; d.fmx[f] = mx; d.fmy[f] = my;
-  d.fcx[f] = cxr; d.fcy[f] = cyr; d.fdL[f] = dL; d.fdR[f] = dR;
+  d.fcx[f] = cxr; d.fcy[f] = cyr; d.fidL[f] = 1.0 / dL; d.fidR[f] = 1.0 / dR;
   d.fdn[f] = fabs((cxr - cxl) * nx + (cyr - cyl) * ny);
   if (!(dL > 0.0) || !(dR > 0.0) || !(S > 0.0)) atomicOr(d.err + 1, 1);
 }
@@ -114,9 +114,18 @@ __device__ __forceinline__ bool cell_live(const Dev& d, int i, int* solve) {
   return true;
 }
 
-// laminar and eddy viscosity of every cell
+// velocity and sound speed of a state, in the order the face spectral radius uses them
+__device__ __forceinline__ void speeds_of(const double* W, double* u, double* v, double* c) {
+  const double p = pressure_of(W[0], W[1], W[2], W[3]);
+  *u = W[1] / W[0];
+  *v = W[2] / W[0];
+  *c = sqrt(GAMMA * p / W[0]);
+}
+
+// laminar and eddy viscosity of every cell, and its velocity and sound speed (read by the
+// face spectral radius of both cells of each face)
 __global__ void __launch_bounds__(CELL_BLOCK) k_prep(Dev d) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, s;
+  int i = (d.g_blk0 + blockIdx.x) * CELL_BLOCK + threadIdx.x, s;
   if (!cell_live(d, i, &s)) return;
   const DevFlow& fl = d.flow[s];
   int n = d.nc_pad;
@@ -124,6 +133,10 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_prep(Dev d) {
   double mu = viscosity(fl, lambda_of(r, mx, my, E));
   d.mu_l[i] = mu;
   d.mu_t[i] = eddy_viscosity(fl, r, nut, mu);
+  const double Wc[4] = {r, mx, my, E};
+  double u, v, c;
+  speeds_of(Wc, &u, &v, &c);
+  d.pu[i] = u; d.pv[i] = v; d.pc[i] = c;
 }
 
 // state of the cell across face f (ghost on a boundary)
@@ -136,19 +149,17 @@ __device__ __forceinline__ void across_W(const Dev& d, int f, int j, double* Wk)
   }
 }
 
-// face spectral radius lambda_f = |Vbar.n| + cbar (+ viscous term), always evaluated with
-// the face's own left/right order so both cells get the same bits
-__device__ __forceinline__ double face_lambda(const DevFlow& fl, const double* WL, const double* WR,
+// face spectral radius lambda_f = |Vbar.n| + cbar (+ viscous term) from the velocities and
+// sound speeds of the two sides, always in the face's own left/right order so both cells
+// get the same bits
+__device__ __forceinline__ double face_lambda(const DevFlow& fl, double uL, double vL, double cL, double rL,
+                                              double uR, double vR, double cR, double rR,
                                               double muL, double mtL, double muR, double mtR,
                                               double nx, double ny, double dn) {
-  double pL = pressure_of(WL[0], WL[1], WL[2], WL[3]);
-  double pR = pressure_of(WR[0], WR[1], WR[2], WR[3]);
-  double uL = WL[1] / WL[0], vL = WL[2] / WL[0], cL = sqrt(GAMMA * pL / WL[0]);
-  double uR = WR[1] / WR[0], vR = WR[2] / WR[0], cR = sqrt(GAMMA * pR / WR[0]);
   double ub = 0.5 * (uL + uR), vb = 0.5 * (vL + vR), cb = 0.5 * (cL + cR);
   double lam = fabs(ub * nx + vb * ny) + cb;
   if (fl.visc_sr) {
-    double mub = 0.5 * (muL + muR), mtb = 0.5 * (mtL + mtR), rb = 0.5 * (WL[0] + WR[0]);
+    double mub = 0.5 * (muL + muR), mtb = 0.5 * (mtL + mtR), rb = 0.5 * (rL + rR);
     lam += 2.0 * (mub + mtb) * GAMMA / (rb * fl.prandtl * dn);
   }
   return lam;
@@ -157,42 +168,47 @@ __device__ __forceinline__ double face_lambda(const DevFlow& fl, const double* W
 // per face: the ghost state of a boundary face (Section II.E) and the face spectral
 // radius lambda_f of Eq. 21 (computed once per face, read by both cells' Lambda sums)
 __global__ void k_ghost(Dev d) {
-  int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= d.nf) return;
+  int f = d.g_face0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= d.g_face0 + d.g_nface) return;
   int s = d.fsolve[f];
   if (d.st[s].state != 0) return;
   const DevFlow& fl = d.flow[s];
   const int L = d.fL[f], R = d.fR[f], n = d.nc_pad;
-  double WL[5], WR[5], muR, mtR;
-  for (int v = 0; v < 5; v++) WL[v] = d.W[v * n + L];
+  double muR, mtR, uR, vR, cR, rR;
   if (R < 0) {
+    double WL[5], WR[5];
+    for (int v = 0; v < 5; v++) WL[v] = d.W[v * n + L];
     ghost_state(fl, d.fbc[f], d.fnx[f], d.fny[f], WL, WR);
     for (int v = 0; v < 5; v++) d.G[v * d.nf + f] = WR[v];
     muR = viscosity(fl, lambda_of(WR[0], WR[1], WR[2], WR[3]));
     mtR = eddy_viscosity(fl, WR[0], WR[4], muR);
     d.Gmu[f] = muR;
     d.Gmu[d.nf + f] = mtR;
+    speeds_of(WR, &uR, &vR, &cR);
+    rR = WR[0];
   } else {
-    for (int v = 0; v < 5; v++) WR[v] = d.W[v * n + R];
     muR = d.mu_l[R];
     mtR = d.mu_t[R];
+    uR = d.pu[R]; vR = d.pv[R]; cR = d.pc[R]; rR = d.W[R];
   }
-  d.lam_f[f] = face_lambda(fl, WL, WR, d.mu_l[L], d.mu_t[L], muR, mtR, d.fnx[f], d.fny[f], d.fdn[f]);
+  d.lam_f[f] = face_lambda(fl, d.pu[L], d.pv[L], d.pc[L], d.W[L], uR, vR, cR, rR, d.mu_l[L], d.mu_t[L], muR, mtR,
+                           d.fnx[f], d.fny[f], d.fdn[f]);
 }
 
 void launch_prep(const Dev& d, cudaStream_t s) {
-  k_prep<<<d.n_cell_blocks, CELL_BLOCK, 0, s>>>(d);
+  k_prep<<<d.g_nblk, CELL_BLOCK, 0, s>>>(d);
 }
 
 void launch_ghost(const Dev& d, cudaStream_t s) {
-  if (d.nf) k_ghost<<<(d.nf + 127) / 128, 128, 0, s>>>(d);
+  if (d.g_nface) k_ghost<<<(d.g_nface + 127) / 128, 128, 0, s>>>(d);
 }
 
 // Least-squares gradients (Eq. 7) of the conserved variables over the face neighbours
 // (ghosts included), the limiter of Eq. 9-10, the vorticity for SA, Lambda_i from the face
 // spectral radii and the per-solve minimum explicit time step (Eq. 23).
 __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, s = -1;
+  const int blk = d.g_blk0 + blockIdx.x;
+  int i = blk * CELL_BLOCK + threadIdx.x, s = -1;
   bool live = cell_live(d, i, &s);
   double dtc = DBL_MAX;
   if (live) {
@@ -225,12 +241,13 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
       Lam += 0.5 * d.lam_f[f] * d.fS[f];
     }
     double det = A00 * A11 - A01 * A01;
+    const double idet = 1.0 / det;
     double area = d.area[i];
     double b[8];
 #pragma unroll
     for (int v = 0; v < 4; v++) {
-      b[2 * v] = (A11 * r0[v] - A01 * r1[v]) / det;
-      b[2 * v + 1] = (A00 * r1[v] - A01 * r0[v]) / det;
+      b[2 * v] = (A11 * r0[v] - A01 * r1[v]) * idet;
+      b[2 * v + 1] = (A00 * r1[v] - A01 * r0[v]) * idet;
       d.grad[(2 * v) * n + i] = b[2 * v];
       d.grad[(2 * v + 1) * n + i] = b[2 * v + 1];
     }
@@ -238,7 +255,9 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
     if (fl.limiter == 1) {
       // Barth-Jespersen: the smallest ratio over the vertices comes from the largest
       // excursion of each sign (correctly rounded division is monotone in the divisor),
-      // so two divisions per variable give the same bits as one per vertex
+      // so two divisions per variable give the same bits as one per vertex; and a
+      // correctly rounded x / y with 0 < x < y stays below 1, so min(1, x / y) is 1
+      // exactly when x >= y and the division is needed only where the limiter acts
       double up[4] = {0, 0, 0, 0}, dn[4] = {0, 0, 0, 0};
       for (int k = d.cn_ptr[i]; k < d.cn_ptr[i + 1]; k++) {
         int nd = d.cn_node[k];
@@ -252,8 +271,9 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
       }
 #pragma unroll
       for (int v = 0; v < 4; v++) {
-        if (up[v] > 0.0) phi[v] = fmin(phi[v], fmin(1.0, (wmax[v] - Wi[v]) / up[v]));
-        if (dn[v] < 0.0) phi[v] = fmin(phi[v], fmin(1.0, (wmin[v] - Wi[v]) / dn[v]));
+        const double hi = wmax[v] - Wi[v], lo = wmin[v] - Wi[v];
+        if (up[v] > 0.0 && hi < up[v]) phi[v] = fmin(phi[v], hi / up[v]);
+        if (dn[v] < 0.0 && lo > dn[v]) phi[v] = fmin(phi[v], lo / dn[v]);
       }
     } else if (fl.limiter == 2) {
       double h = sqrt(area);
@@ -275,9 +295,10 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
     }
 #pragma unroll
     for (int v = 0; v < 4; v++) d.phi[v * n + i] = phi[v];
-    double u = Wi[1] / Wi[0], vv = Wi[2] / Wi[0];
-    double dudy = (b[3] - u * b[1]) / Wi[0];
-    double dvdx = (b[4] - vv * b[0]) / Wi[0];
+    const double ir = 1.0 / Wi[0];
+    double u = Wi[1] * ir, vv = Wi[2] * ir;
+    double dudy = (b[3] - u * b[1]) * ir;
+    double dvdx = (b[4] - vv * b[0]) * ir;
     d.omega[i] = fabs(dvdx - dudy);
     d.Lam[i] = Lam;
     dtc = fl.cfl_exp * area / Lam;
@@ -292,7 +313,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
     m = threadIdx.x < CELL_BLOCK / 32 ? red[threadIdx.x] : DBL_MAX;
     for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (threadIdx.x == 0 && m < DBL_MAX) {
-      int bs = d.cell_solve[blockIdx.x * CELL_BLOCK];
+      int bs = d.cell_solve[blk * CELL_BLOCK];
       // positive doubles order like their bit patterns
       if (bs >= 0) atomicMin(d.dt_bits + bs, (unsigned long long)__double_as_longlong(m));
     }
@@ -300,14 +321,15 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
 }
 
 void launch_gradient(const Dev& d, cudaStream_t s) {
-  k_gradient<<<d.n_cell_blocks, CELL_BLOCK, 0, s>>>(d);
+  k_gradient<<<d.g_nblk, CELL_BLOCK, 0, s>>>(d);
 }
 
 // Residual M_i = -(1/dt) sum over the faces of cell i (ascending face order) of the signed
 // face flux (Eq. 16), the SA right-hand side Omega Sr + R (Eq. 27-28a), the SA diagonal
 // without its time term, and per-block partial norms of M_rho.
 __global__ void __launch_bounds__(CELL_BLOCK) k_residual(Dev d) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, s = -1;
+  const int blk = d.g_blk0 + blockIdx.x;
+  int i = blk * CELL_BLOCK + threadIdx.x, s = -1;
   bool live = cell_live(d, i, &s);
   double rmax = 0.0, r2 = 0.0;
   if (live) {
@@ -329,38 +351,43 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_residual(Dev d) {
         sad += d.sa_a[3 * nf + f];
       }
     }
+    const double idt = 1.0 / dt;
 #pragma unroll
-    for (int v = 0; v < 4; v++) d.M[v * n + i] = -acc[v] / dt;
+    for (int v = 0; v < 4; v++) d.M[v * n + i] = -acc[v] * idt;
     double area = d.area[i];
+    const double iarea = 1.0 / area;
     double m4 = 0.0, fw = 0.0, sdiag = 0.0;
     if (fl.sa_on) {
-      const double k2 = SA_KAPPA * SA_KAPPA;
+      // Eq. 28a with SA-noft2 and the 2012 clipping of S~; the wall distance enters through
+      // 1/d, the viscosity ratio through chi = nu~ rho / mu, and x^(1/6) is cbrt(sqrt(x))
+      const double ik2 = 1.0 / (SA_KAPPA * SA_KAPPA);
       double r = d.W[i], nut = d.W[4 * n + i];
-      double nu = d.mu_l[i] / r;
-      double chi = nut / nu, c3 = chi * chi * chi;
+      double chi = nut * r / d.mu_l[i], c3 = chi * chi * chi;
       double fv1 = c3 / (c3 + SA_CV1 * SA_CV1 * SA_CV1);
       double fv2 = 1.0 - chi / (1.0 + chi * fv1);
-      double om = d.omega[i], dw = d.wall_d[i];
-      double Sbar = nut * fv2 / (k2 * dw * dw);
+      double om = d.omega[i], idw = 1.0 / d.wall_d[i];
+      double nd2 = nut * idw * idw * ik2;              // nu~ / (kappa^2 d^2)
+      double Sbar = fv2 * nd2;
       double St = (Sbar >= -SA_CV2 * om)
                       ? om + Sbar
                       : om + om * (SA_CV2 * SA_CV2 * om + SA_CV3 * Sbar) / ((SA_CV3 - 2.0 * SA_CV2) * om - Sbar);
-      double rr = (nut < 10.0 * St * k2 * dw * dw) ? nut / (St * k2 * dw * dw) : 10.0;
+      double rr = (nd2 < 10.0 * St) ? nd2 / St : 10.0;
       double r2_ = rr * rr, r6 = r2_ * r2_ * r2_;
       double g = rr + SA_CW2 * (r6 - rr);
       double g2 = g * g, g6 = g2 * g2 * g2;
       const double c6 = SA_CW3 * SA_CW3 * SA_CW3 * SA_CW3 * SA_CW3 * SA_CW3;
-      fw = g * pow((1.0 + c6) / (g6 + c6), 1.0 / 6.0);
-      double Sr = SA_CB1 * St * nut - SA_CW1 * fw * (nut / dw) * (nut / dw);
+      fw = g * cbrt(sqrt((1.0 + c6) / (g6 + c6)));
+      double nd = nut * idw;
+      double Sr = SA_CB1 * St * nut - SA_CW1 * fw * nd * nd;
       m4 = area * Sr + acc[4];
-      sdiag = sad + area * 2.0 * SA_CW1 * fw * nut / (dw * dw);
+      sdiag = sad + area * 2.0 * SA_CW1 * fw * nut * idw * idw;
     }
     d.M[4 * n + i] = m4;
     d.fw[i] = fw;
     d.sa_diag[i] = sdiag;
     double mr = d.M[i];
     rmax = fabs(mr);
-    double q = mr / area;
+    double q = mr * iarea;
     r2 = q * q;
   }
   __shared__ double smax[CELL_BLOCK / 32], ssum[CELL_BLOCK / 32];
@@ -373,19 +400,19 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_residual(Dev d) {
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0;
     for (int w = 0; w < CELL_BLOCK / 32; w++) { a = fmax(a, smax[w]); b += ssum[w]; }
-    d.part[blockIdx.x] = a;
-    d.part[d.n_cell_blocks + blockIdx.x] = b;
+    d.part[blk] = a;
+    d.part[d.n_cell_blocks + blk] = b;
   }
 }
 
 void launch_residual(const Dev& d, cudaStream_t s) {
-  k_residual<<<d.n_cell_blocks, CELL_BLOCK, 0, s>>>(d);
+  k_residual<<<d.g_nblk, CELL_BLOCK, 0, s>>>(d);
 }
 
 // per-solve norms in fixed block order, CFL adaptation (Eq. 25), stopping rule
 __global__ void k_norms(Dev d) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= d.n_solves) return;
+  int s = d.g_solve0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.g_solve0 + d.g_nsolve) return;
   SolveState& st = d.st[s];
   if (st.state != 0) return;
   const DevFlow& fl = d.flow[s];
@@ -397,6 +424,9 @@ __global__ void k_norms(Dev d) {
   st.dt = __longlong_as_double((long long)d.dt_bits[s]);
   st.res_inf = rmax;
   st.res_l2 = sqrt(r2 / (double)(st.cell_end - st.cell_begin));
+  double* h = d.hist + ((size_t)s * HIST + (size_t)(st.iter % HIST)) * 2;   // residual history
+  h[0] = st.res_l2;
+  h[1] = st.res_inf;
   if (st.iter == 0) {
     st.cfl = fl.cfl_init;
     st.res_l2_first = st.res_l2;
@@ -415,12 +445,12 @@ __global__ void k_norms(Dev d) {
 }
 
 void launch_norms(const Dev& d, cudaStream_t s) {
-  k_norms<<<(d.n_solves + 63) / 64, 64, 0, s>>>(d);
+  k_norms<<<(d.g_nsolve + 63) / 64, 64, 0, s>>>(d);
 }
 
 __global__ void k_end_iter(Dev d) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= d.n_solves) return;
+  int s = d.g_solve0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.g_solve0 + d.g_nsolve) return;
   SolveState& st = d.st[s];
   if (st.state != 0) return;
   st.eq40 = __longlong_as_double((long long)d.eq40_bits[s]);
@@ -435,7 +465,7 @@ __global__ void k_end_iter(Dev d) {
 }
 
 void launch_end_iter(const Dev& d, cudaStream_t s) {
-  k_end_iter<<<(d.n_solves + 63) / 64, 64, 0, s>>>(d);
+  k_end_iter<<<(d.g_nsolve + 63) / 64, 64, 0, s>>>(d);
 }
 
 }  // namespace igks

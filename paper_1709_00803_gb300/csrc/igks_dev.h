@@ -60,6 +60,7 @@ struct Dev {
   double* phi;              // [4][nc_pad]
   double* omega;            // [nc_pad] vorticity magnitude (SA)
   double* mu_l; double* mu_t;
+  double* pu; double* pv; double* pc;   // [nc_pad] velocity and sound speed of every cell (k_prep)
   double* Lam;              // [nc_pad] sum over faces of (Lambda_c)_ij
   double* M;                // [5][nc_pad]
   double* fw;               // [nc_pad]
@@ -73,7 +74,7 @@ struct Dev {
   const int* bface;         // [nbf] boundary face ids
   double* fS; double* fnx; double* fny; double* fmx; double* fmy;
   double* fcx; double* fcy; // centre across the face (neighbour or ghost)
-  double* fdL; double* fdR; double* fdn;   // normal distances centre->face, centre->centre
+  double* fidL; double* fidR; double* fdn; // reciprocal normal distances centre->face; centre->centre
   double* lam_f;            // [nf]
   double* F;                // [6][nf]
   double* sa_a;             // [4][nf]: aLR, aRL, diag L, diag R
@@ -124,9 +125,16 @@ struct Dev {
   unsigned long long* eq40_bits; // [n_solves] atomic max of the Eq. 40 ratio
   int* bad;                      // [n_solves] divergence flag of the current update
   double* part;                  // [2][n_blocks] residual norm partials per cell block
+  double* hist;                  // [n_solves][HIST][2] residual norms of the last HIST iterations
   int n_cell_blocks;
   int flux_block;                // threads per block of the flux kernel (<= 128)
   int* err;                      // [4] device error flags (mesh orientation, area)
+  // The range one launch of an iteration kernel covers: a group of consecutive solves
+  // (the whole context unless the solves are split into groups that run on streams of
+  // their own). Per-cell kernels take blocks [g_blk0, g_blk0 + g_nblk) of CELL_BLOCK
+  // cells, per-face kernels faces [g_face0, g_face0 + g_nface), per-solve kernels and the
+  // narrow sweeps solves [g_solve0, g_solve0 + g_nsolve).
+  int g_blk0, g_nblk, g_face0, g_nface, g_solve0, g_nsolve;
 };
 
 // ---- launches (igks_kernels.cu / igks_flux.cu) ----
@@ -150,5 +158,6 @@ constexpr int RING = 1024;           // shared-memory ring of the narrow sweeps 
 constexpr int PF_E = 4;              // stencil entries held per prefetched sweep position
 constexpr int NARROW_THREADS = 256;  // block of the narrow sweeps (one thread per cell of a level)
 constexpr int WIDE_MAX_LEVELS = 64;  // automatic choice: wide schedule up to this many levels
+constexpr int HIST = 1024;           // iterations of residual history kept per solve
 
 }  // namespace igks

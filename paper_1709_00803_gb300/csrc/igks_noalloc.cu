@@ -89,9 +89,14 @@ extern "C" int igks_residual_norms_noalloc(const double* m_rho, const double* ar
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+  if (e != cudaSuccess) {
     g_err = std::string("igks_residual_norms_noalloc: cudaGetDevice: ") + cudaGetErrorString(e);
     return IGKS_ECUDA;
+  }
+  if (dev < 0 || dev >= MAX_DEVICES) {
+    g_err = "igks_residual_norms_noalloc: device ordinal " + std::to_string(dev) +
+            " is beyond the " + std::to_string(MAX_DEVICES) + " devices it keeps a scratch address for";
+    return IGKS_EINVAL;
   }
   double* scratch = nullptr;
   {

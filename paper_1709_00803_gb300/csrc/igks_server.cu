@@ -39,6 +39,7 @@ struct Request {
   // state of a live solve moved out of a cohort that is being freed
   bool carried = false;
   std::vector<double> W;
+  std::vector<double> W0;   // the request's starting state (empty: free stream)
   double scal[5] = {0, 0, 0, 0, 0};
 };
 
@@ -154,6 +155,7 @@ static int build_cohort(igks_server* s, std::vector<Request>& reqs, Cohort& out)
       if (!rc) rc = igks_set_scalars(ctx, m.sid, m.req.scal);
     } else {
       rc = igks_init_freestream(ctx, m.sid);
+      if (!rc && !m.req.W0.empty()) rc = igks_set_fields(ctx, m.sid, m.req.W0.data());
     }
     if (rc) break;
   }
@@ -169,6 +171,8 @@ static int build_cohort(igks_server* s, std::vector<Request>& reqs, Cohort& out)
     m.req.carried = false;
     m.req.W.clear();
     m.req.W.shrink_to_fit();
+    m.req.W0.clear();
+    m.req.W0.shrink_to_fit();
   }
   out.serial = s->next_cohort++;
   return 0;
@@ -367,6 +371,12 @@ int igks_server_submit(igks_server* s, const igks_request* q, int64_t* id) {
   r.face_nodes.assign(q->face_nodes, q->face_nodes + 2 * (size_t)r.nf);
   r.face_cells.assign(q->face_cells, q->face_cells + 2 * (size_t)r.nf);
   r.face_bc.assign(q->face_bc, q->face_bc + r.nf);
+  if (q->W0) {
+    for (int i = 0; i < r.nc; i++)
+      if (!(q->W0[i] > 0.0) || !std::isfinite(q->W0[3 * (size_t)r.nc + i]))
+        return sfail(s, IGKS_EINVAL, "non-physical starting state");
+    r.W0.assign(q->W0, q->W0 + 5 * (size_t)r.nc);
+  }
   r.flow = q->flow;
   r.tag = q->tag;
   r.id = s->next_id++;

@@ -74,7 +74,7 @@ __device__ __forceinline__ void bwd_acc(T* acc, T sx, T sy, T sl, T sa, const T*
 // ---- pre-pass: per-cell constants and the signed stencil of every cell ----
 template <class T>
 __global__ void __launch_bounds__(CELL_BLOCK) k_sweep_prep(Dev d) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (d.g_blk0 + blockIdx.x) * CELL_BLOCK + threadIdx.x;
   if (i >= d.nc_pad) return;
   const int s = d.cell_solve[i];
   if (s < 0 || d.st[s].state != 0 || d.flow[s].scheme == 1) return;   // explicit solves: no sweeps
@@ -83,26 +83,33 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_sweep_prep(Dev d) {
   const double cfl = d.st[s].cfl;
   const double Lam = d.Lam[i];
   const double r = d.W[i], mx = d.W[n + i], my = d.W[2 * n + i], E = d.W[3 * n + i];
-  const double u = mx / r, v = my / r;
+  const double u = d.pu[i], v = d.pv[i];          // mx / r, my / r (k_prep)
   const double p = (GAMMA - 1.0) * (E - 0.5 * (mx * u + my * v));
-  T* c = (T*)d.sw_cell;
-  c[i] = (T)(1.0 / (Lam / cfl + Lam));                                  // 1/D (Eq. 20, 24)
-  c[n + i] = fl.sa_on ? (T)(1.0 / (Lam / cfl + d.sa_diag[i])) : (T)0;   // 1/a_ii (Eq. 32)
-  c[2 * n + i] = (T)u;
-  c[3 * n + i] = (T)v;
-  c[4 * n + i] = (T)(E + p);
+  T cc[5];
+  cc[0] = (T)(1.0 / (Lam / cfl + Lam));                                  // 1/D (Eq. 20, 24)
+  cc[1] = fl.sa_on ? (T)(1.0 / (Lam / cfl + d.sa_diag[i])) : (T)0;       // 1/a_ii (Eq. 32)
+  cc[2] = (T)u;
+  cc[3] = (T)v;
+  cc[4] = (T)(E + p);
+  const bool wide = d.wide != 0;
+  if (wide) {   // the one-launch-per-level sweeps read the cell constants in cell order
+    T* c = (T*)d.sw_cell;
+#pragma unroll
+    for (int q = 0; q < 5; q++) c[q * n + i] = cc[q];
+  }
   // position-ordered records of the narrow schedule
-  {
-    const int P = d.npos, pf = d.pos_f[i], pb = d.pos_b[i];
+  const int P = d.npos, pf = d.pos_f[i], pb = d.pos_b[i];
+  const bool csr_f = d.cnt_f[pf] < 0, csr_b = d.cnt_b[pb] < 0;   // more entries than a record holds
+  if (!wide) {
     T* rf = (T*)d.rec_f;
     T* rb = (T*)d.rec_b;
 #pragma unroll
-    for (int v = 0; v < 5; v++) rf[v * P + pf] = (T)d.M[v * n + i];
+    for (int q = 0; q < 5; q++) rf[q * P + pf] = (T)d.M[q * n + i];
     rf[5 * P + pf] = (T)r; rf[6 * P + pf] = (T)mx; rf[7 * P + pf] = (T)my;
 #pragma unroll
-    for (int v = 0; v < 5; v++) { rf[(8 + v) * P + pf] = c[v * n + i]; rb[(5 + v) * P + pb] = c[v * n + i]; }
+    for (int q = 0; q < 5; q++) { rf[(8 + q) * P + pf] = cc[q]; rb[(5 + q) * P + pb] = cc[q]; }
 #pragma unroll
-    for (int v = 0; v < 5; v++) rb[v * P + pb] = (T)d.W[v * n + i];
+    for (int q = 0; q < 5; q++) rb[q * P + pb] = (T)d.W[q * n + i];
   }
   T* sc = (T*)d.sw_st;
   const int nnz = d.nnz;
@@ -112,30 +119,33 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_sweep_prep(Dev d) {
     const int j = own ? d.fR[f] : d.fL[f];
     const double hS = 0.5 * d.fS[f];
     const double sg = own ? hS : -hS;
-    d.sw_j[k] = j;                                    // -1 on a boundary face
-    sc[k] = (T)(sg * d.fnx[f]);
-    sc[nnz + k] = (T)(sg * d.fny[f]);
-    sc[2 * nnz + k] = (T)(hS * d.lam_f[f]);
-    sc[3 * nnz + k] = (T)d.sa_a[(own ? 0 : 1) * nf + f];
-    // the same coefficients in sweep-position order for the narrow schedule
-    const int ef = d.cf_to_fs[k], eb = d.cf_to_bs[k];
-    if (ef >= 0) {
-      T* o = (T*)d.sc_f;
-      o[ef] = sc[k]; o[d.nfs + ef] = sc[nnz + k]; o[2 * d.nfs + ef] = sc[2 * nnz + k]; o[3 * d.nfs + ef] = sc[3 * nnz + k];
-    }
-    if (eb >= 0) {
-      T* o = (T*)d.sc_b;
-      o[eb] = sc[k]; o[d.nbs + eb] = sc[nnz + k]; o[2 * d.nbs + eb] = sc[2 * nnz + k]; o[3 * d.nbs + eb] = sc[3 * nnz + k];
-    }
-    const size_t PE = (size_t)PF_E * d.npos;
-    const int xf = d.cf_to_ef[k], xb = d.cf_to_eb[k];
-    if (xf >= 0) {
-      T* o = (T*)d.ec_f;
-      o[xf] = sc[k]; o[PE + xf] = sc[nnz + k]; o[2 * PE + xf] = sc[2 * nnz + k]; o[3 * PE + xf] = sc[3 * nnz + k];
-    }
-    if (xb >= 0) {
-      T* o = (T*)d.ec_b;
-      o[xb] = sc[k]; o[PE + xb] = sc[nnz + k]; o[2 * PE + xb] = sc[2 * nnz + k]; o[3 * PE + xb] = sc[3 * nnz + k];
+    const T e0 = (T)(sg * d.fnx[f]), e1 = (T)(sg * d.fny[f]), e2 = (T)(hS * d.lam_f[f]);
+    const T e3 = (T)d.sa_a[(own ? 0 : 1) * nf + f];
+    if (wide) {   // the cell-ordered stencil of the one-launch-per-level sweeps
+      d.sw_j[k] = j;                                  // -1 on a boundary face
+      sc[k] = e0; sc[nnz + k] = e1; sc[2 * nnz + k] = e2; sc[3 * nnz + k] = e3;
+    } else {
+      // the narrow schedule: up to PF_E entries per position in its record, the rest of a
+      // larger stencil in the position-ordered CSR lists
+      const int ef = d.cf_to_fs[k], eb = d.cf_to_bs[k];
+      if (ef >= 0 && csr_f) {
+        T* o = (T*)d.sc_f;
+        o[ef] = e0; o[d.nfs + ef] = e1; o[2 * d.nfs + ef] = e2; o[3 * d.nfs + ef] = e3;
+      }
+      if (eb >= 0 && csr_b) {
+        T* o = (T*)d.sc_b;
+        o[eb] = e0; o[d.nbs + eb] = e1; o[2 * d.nbs + eb] = e2; o[3 * d.nbs + eb] = e3;
+      }
+      const size_t PE = (size_t)PF_E * d.npos;
+      const int xf = d.cf_to_ef[k], xb = d.cf_to_eb[k];
+      if (xf >= 0) {
+        T* o = (T*)d.ec_f;
+        o[xf] = e0; o[PE + xf] = e1; o[2 * PE + xf] = e2; o[3 * PE + xf] = e3;
+      }
+      if (xb >= 0) {
+        T* o = (T*)d.ec_b;
+        o[xb] = e0; o[PE + xb] = e1; o[2 * PE + xb] = e2; o[3 * PE + xb] = e3;
+      }
     }
     // the ghost state of a wall or symmetry face in the form the backward sweep's flux
     // increment takes it (its only ghost entries), so the sweep itself does no FP64 work
@@ -232,8 +242,9 @@ __device__ __forceinline__ void bwd_cell(const Dev& d, int i, bool sa_on) {
 // chain, and its FP64 square roots and division are spread over the whole GPU.
 template <class T>
 __global__ void __launch_bounds__(CELL_BLOCK) k_update(Dev d) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = d.cell_solve[blockIdx.x * CELL_BLOCK];   // every block lies in one solve
+  const int blk = d.g_blk0 + blockIdx.x;
+  const int i = blk * CELL_BLOCK + threadIdx.x;
+  const int s = d.cell_solve[blk * CELL_BLOCK];   // every block lies in one solve
   double eq40 = 0.0;
   int bad = 0;
   const bool live = (i < d.nc_pad) && d.cell_solve[i] >= 0 && d.st[d.cell_solve[i]].state == 0;
@@ -475,7 +486,7 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_sweep_fwd_narrow(Dev d) {
   T* ring = (T*)smem_raw;
   FwdRec<T>* stage = (FwdRec<T>*)(smem_raw + (size_t)13 * RING * sizeof(T));
   FwdRec<T>* st = stage + threadIdx.x;               // staged record of this thread's next position
-  const int s = blockIdx.x / C, r = blockIdx.x % C;  // one cluster of C blocks per solve
+  const int s = d.g_solve0 + blockIdx.x / C, r = blockIdx.x % C;  // one cluster of C blocks per solve
   if (d.st[s].state != 0 || d.flow[s].scheme == 1) return;   // uniform over the cluster
   if constexpr (C > 1) cg::this_cluster().sync();    // every block runs before any remote read
   const bool sa_on = d.flow[s].sa_on;
@@ -634,7 +645,7 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_sweep_bwd_narrow(Dev d) {
   T* ring = (T*)smem_raw;
   BwdRec<T>* stage = (BwdRec<T>*)(smem_raw + (size_t)13 * RING * sizeof(T));
   BwdRec<T>* st = stage + threadIdx.x;
-  const int s = blockIdx.x / C, r = blockIdx.x % C;
+  const int s = d.g_solve0 + blockIdx.x / C, r = blockIdx.x % C;
   if (d.st[s].state != 0 || d.flow[s].scheme == 1) return;
   if constexpr (C > 1) cg::this_cluster().sync();
   const bool sa_on = d.flow[s].sa_on;
@@ -691,8 +702,8 @@ __global__ void k_sweep_bwd_level(Dev d, int b, int e) {
 constexpr int WIDE_BLOCK = 128;
 
 void launch_update(const Dev& d, int precision, cudaStream_t s) {
-  if (precision == 1) k_update<float><<<d.n_cell_blocks, CELL_BLOCK, 0, s>>>(d);
-  else k_update<double><<<d.n_cell_blocks, CELL_BLOCK, 0, s>>>(d);
+  if (precision == 1) k_update<float><<<d.g_nblk, CELL_BLOCK, 0, s>>>(d);
+  else k_update<double><<<d.g_nblk, CELL_BLOCK, 0, s>>>(d);
 }
 
 // dynamic shared memory of the narrow sweeps: the ring plus one staged record per thread
@@ -719,11 +730,11 @@ static void launch_narrow(bool fwd, const Dev& d, int threads, cudaStream_t s) {
   void (*k)(Dev) = fwd ? k_sweep_fwd_narrow<T, C> : k_sweep_bwd_narrow<T, C>;
   const size_t smem = fwd ? fwd_smem<T>() : bwd_smem<T>();
   if (C == 1) {
-    k<<<d.n_solves, threads, smem, s>>>(d);
+    k<<<d.g_nsolve, threads, smem, s>>>(d);
     return;
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(d.n_solves * C));
+  cfg.gridDim = dim3((unsigned)(d.g_nsolve * C));
   cfg.blockDim = dim3((unsigned)threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -748,8 +759,8 @@ static void launch_narrow_c(bool fwd, const Dev& d, int threads, cudaStream_t s)
 }
 
 void launch_sweep_prep(const Dev& d, int precision, cudaStream_t s) {
-  if (precision == 1) k_sweep_prep<float><<<d.n_cell_blocks, CELL_BLOCK, 0, s>>>(d);
-  else k_sweep_prep<double><<<d.n_cell_blocks, CELL_BLOCK, 0, s>>>(d);
+  if (precision == 1) k_sweep_prep<float><<<d.g_nblk, CELL_BLOCK, 0, s>>>(d);
+  else k_sweep_prep<double><<<d.g_nblk, CELL_BLOCK, 0, s>>>(d);
 }
 
 void launch_sweep_fwd(const Dev& d, int precision, int threads, cudaStream_t s) {

@@ -28,7 +28,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
                 ("check_every", C.c_int32), ("use_graph", C.c_int32), ("sweep_threads", C.c_int32),
                 ("timing", C.c_int32), ("sweep_mode", C.c_int32), ("sweep_cluster", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("groups", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class Flow(C.Structure):
@@ -43,7 +43,7 @@ class Flow(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("sweep_threads", C.c_int32), ("flux_block", C.c_int32), ("sweep_mode", C.c_int32),
-                ("sweep_cluster", C.c_int32), ("ms_per_iter", C.c_float)]
+                ("sweep_cluster", C.c_int32), ("ms_per_iter", C.c_float), ("groups", C.c_int32)]
 
 
 class Status(C.Structure):
@@ -65,7 +65,8 @@ class ServerOptions(C.Structure):
 class Request(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("xy", C.c_void_p), ("n_cells", C.c_int32), ("cell_ptr", C.c_void_p),
                 ("cell_nodes", C.c_void_p), ("n_faces", C.c_int32), ("face_nodes", C.c_void_p),
-                ("face_cells", C.c_void_p), ("face_bc", C.c_void_p), ("flow", Flow), ("tag", C.c_int64)]
+                ("face_cells", C.c_void_p), ("face_bc", C.c_void_p), ("flow", Flow), ("tag", C.c_int64),
+                ("W0", C.c_void_p)]
 
 
 class Result(C.Structure):
@@ -122,7 +123,10 @@ def lib():
         L.igks_kernel_name.restype = C.c_char_p
         L.igks_residual_norms_noalloc.argtypes = [vp, vp, i32, vp, vp]
         L.igks_residual_norms_noalloc.restype = C.c_int32
+        L.igks_fp64_probe.argtypes = [i32, dp]
         L.igks_autotune.argtypes = [vp, i32, P(Tuning)]
+        L.igks_set_launch.argtypes = [vp, P(Tuning)]
+        L.igks_get_history.argtypes = [vp, i32, i32, dp, ip]
         L.igks_autotune.restype = C.c_int32
         L.igks_order_cells.argtypes = [i32, i32, ip, i32, ip, ip]
         L.igks_order_cells.restype = C.c_int32
@@ -157,6 +161,15 @@ def library_path() -> str:
 
 
 NOALLOC_MAX_CELLS = 1 << 20
+
+
+def fp64_probe(device: int = 0) -> float:
+    """Measured FP64 rate of the device in TFLOP/s (igks_fp64_probe)."""
+    t = C.c_double()
+    rc = lib().igks_fp64_probe(device, C.byref(t))
+    if rc != OK:
+        raise IgksError(rc, "igks_fp64_probe failed")
+    return t.value
 
 
 def residual_norms_noalloc(m_rho_ptr: int, area_ptr: int, n_cells: int, out_ptr: int, stream: int = 0) -> int:
@@ -206,10 +219,10 @@ class Context:
     """One igks_ctx: a set of steady solves resident on one GPU."""
 
     def __init__(self, precision=PREC_FP64, device=0, stream=None, check_every=20, use_graph=1,
-                 sweep_threads=0, timing=0, sweep_mode=0, sweep_cluster=0):
+                 sweep_threads=0, timing=0, sweep_mode=0, sweep_cluster=0, groups=0):
         o = Options(precision=precision, device=device, stream=stream, check_every=check_every,
                     use_graph=use_graph, sweep_threads=sweep_threads, timing=timing, sweep_mode=sweep_mode,
-                    sweep_cluster=sweep_cluster)
+                    sweep_cluster=sweep_cluster, groups=groups)
         h = C.c_void_p()
         rc = lib().igks_create(C.byref(o), C.byref(h))
         if rc:
@@ -257,6 +270,11 @@ class Context:
         self._check(lib().igks_autotune(self.h, iters_per_trial, C.byref(t)))
         return {k: getattr(t, k) for k, _ in t._fields_}
 
+    def set_launch(self, tuning):
+        """Apply a launch configuration (a dict as autotune() returns)."""
+        t = Tuning(**{k: tuning[k] for k, _ in Tuning._fields_ if k in tuning})
+        self._check(lib().igks_set_launch(self.h, C.byref(t)))
+
     def kernel_times(self):
         ms = (C.c_float * 32)()
         n = C.c_int32()
@@ -293,6 +311,13 @@ class Context:
         out = np.zeros(shapes[which])
         self._check(lib().igks_get_array(self.h, solve, ARR[which], _dp(out)))
         return out
+
+    def get_history(self, solve, cap=1024):
+        """Residual history of a solve: array [n, 3] of (iteration, RMS M_rho/Omega, max |M_rho|)."""
+        out = np.zeros((cap, 3))
+        n = C.c_int32()
+        self._check(lib().igks_get_history(self.h, solve, cap, _dp(out), C.byref(n)))
+        return out[:n.value].copy()
 
     def mesh_info(self, solve):
         o = np.zeros(5, dtype=np.int32)
@@ -356,7 +381,9 @@ class Server:
             raise IgksError(rc, lib().igks_server_last_error(self.h).decode())
         return rc
 
-    def submit(self, mesh, flow, tag=0) -> int:
+    def submit(self, mesh, flow, tag=0, W0=None) -> int:
+        """Queue one steady solve; W0 (optional, [5, n_cells]) is its starting state."""
+        w0 = None if W0 is None else np.ascontiguousarray(W0, dtype=np.float64).reshape(5, mesh.n_cells)
         arrs = (np.ascontiguousarray(mesh.xy, dtype=np.float64).ravel(),
                 np.ascontiguousarray(mesh.cell_ptr, dtype=np.int32),
                 np.ascontiguousarray(mesh.cell_nodes, dtype=np.int32),
@@ -365,7 +392,8 @@ class Server:
                 np.ascontiguousarray(mesh.face_bc, dtype=np.int32))
         xy, cp, cn, fn, fc, fb = (a.ctypes.data for a in arrs)
         r = Request(n_nodes=mesh.n_nodes, xy=xy, n_cells=mesh.n_cells, cell_ptr=cp, cell_nodes=cn,
-                    n_faces=mesh.n_faces, face_nodes=fn, face_cells=fc, face_bc=fb, flow=to_flow(flow), tag=tag)
+                    n_faces=mesh.n_faces, face_nodes=fn, face_cells=fc, face_bc=fb, flow=to_flow(flow), tag=tag,
+                    W0=None if w0 is None else w0.ctypes.data)
         rid = C.c_int64()
         self._check(lib().igks_server_submit(self.h, C.byref(r), C.byref(rid)))
         self._keep[rid.value] = mesh.n_cells

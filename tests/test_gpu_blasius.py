@@ -41,6 +41,39 @@ def test_blasius_shooting_gives_the_known_wall_curvature():
     assert abs(s - 0.332057) < 2e-5
 
 
+def _profile_error(W, xc, yc, nx, ny, re):
+    """max |u/U - f'(eta)| across the layer at the cell column nearest x = 0.5."""
+    xc, yc = xc.reshape(ny, nx), yc.reshape(ny, nx)
+    i = int(np.argmin(np.abs(xc[0] - 0.5)))
+    x = xc[0, i]
+    u = (W[1] / W[0]).reshape(ny, nx)[:, i]
+    eta = yc[:, i] * np.sqrt(re / x)
+    et, fp, _ = blasius()
+    sel = eta <= 8.0
+    return np.abs(u[sel] - np.interp(eta[sel], et, fp)), int(sel.sum()), x
+
+
+def test_oracle_converged_plate_matches_blasius():
+    """The oracle's own fixed point: its converged field on the verification plate (run to
+    Eq. 40 <= 3e-8 by tests/golden/make_converged_fields.py, oracle only) has the Blasius
+    profile across the layer, and its residual there is at the converged level."""
+    import os
+    import oracle as O
+    d = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "converged_blasius_plate.npz"))
+    nx, ny = 64, 64
+    m = G.flat_plate_quads(nx, ny, first=1e-4, name="plate_blasius")
+    fl = F.laminar_plate_flow()
+    o = O.Oracle(m, fl)
+    o.set_W(d["W"])
+    gc = o.get(O.ORA_GEOM_CELL)
+    err, n, x = _profile_error(d["W"], gc[1], gc[2], nx, ny, fl.reynolds)
+    assert n >= 20
+    assert err.max() <= 0.02, (x, err.max())
+    # one more oracle iteration from the stored field changes it by the paper's criterion
+    o.iterate(1)
+    assert o.scalars()["eq40"] <= 3e-8
+
+
 @pytest.mark.gpu
 def test_laminar_plate_profile_matches_blasius():
     from paper_1709_00803_gb300 import igks

@@ -77,3 +77,48 @@ def test_eq40_stopping_rule_matches_oracle():
     if st[sid]["iters"] == it_ref:
         err = _rel_l2(ctx.get_fields(sid)[:4], o.get(O.ORA_W)[:4])
         assert np.all(err <= 1e-10), err
+
+
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"converged_{name}.npz")
+    d = np.load(path)
+    return d["W"], int(d["iters"])
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-9)])
+def test_laminar_plate_converged_fields_match_oracle(precision, tol):
+    """The 64 x 32 laminar flat plate (2048 cells, Ma 0.15, Re 1e5, CFL 100) run from the
+    free stream to density residual 1e-10, against the oracle's own converged field
+    (tests/golden/make_converged_fields.py, ~16.5k oracle iterations): FP64 sweeps within
+    1e-10 relative L2 per conserved variable, FP32 sweeps within 1e-9."""
+    from paper_1709_00803_gb300 import igks
+    W_ref, it_ref = _golden("laminar_plate")
+    m = G.laminar_plate()
+    ctx = igks.Context(precision=precision, check_every=100)
+    sid = ctx.mesh_upload(m); ctx.set_flow(sid, F.laminar_plate_flow()); ctx.init_freestream(sid)
+    rc, st = ctx.iterate(40000)
+    assert rc == igks.CONVERGED and st[sid]["res_l2_rel"] <= 1e-10, st[sid]
+    err = _rel_l2(ctx.get_fields(sid)[:4], W_ref[:4])
+    assert np.all(err <= tol), (precision, err, st[sid]["iters"], it_ref)
+    if precision == 0:
+        assert abs(st[sid]["iters"] - it_ref) <= 1
+
+
+def test_blasius_plate_converged_fields_match_oracle():
+    """The 64 x 64 verification plate run to the paper's criterion (Eq. 40 ratio <= 3e-8)
+    on the FP64 path: the same stopping iteration as the oracle and, when it is the same,
+    fields within 1e-10 relative L2 of the oracle's."""
+    from paper_1709_00803_gb300 import igks
+    W_ref, it_ref = _golden("blasius_plate")
+    m = G.flat_plate_quads(64, 64, first=1e-4, name="plate_blasius")
+    fl = F.laminar_plate_flow()
+    fl.eq40_target = 3e-8
+    ctx = igks.Context(precision=0, check_every=100)
+    sid = ctx.mesh_upload(m); ctx.set_flow(sid, fl); ctx.init_freestream(sid)
+    rc, st = ctx.iterate(40000)
+    assert rc == igks.CONVERGED, st[sid]
+    assert abs(st[sid]["iters"] - it_ref) <= 1
+    if st[sid]["iters"] == it_ref:
+        err = _rel_l2(ctx.get_fields(sid)[:4], W_ref[:4])
+        assert np.all(err <= 1e-10), err
