@@ -25,7 +25,11 @@ __device__ __forceinline__ void rot(const double* g, double nx, double ny, doubl
   o[3] = g[3];
 }
 
-__global__ void __launch_bounds__(128) k_flux(Dev d) {
+#ifndef IGKS_FLUX_MINB
+#define IGKS_FLUX_MINB 1   // resident blocks per SM the register budget is cut for
+#endif
+
+__global__ void __launch_bounds__(128, IGKS_FLUX_MINB) k_flux(Dev d) {
   const int f = d.g_face0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= d.g_face0 + d.g_nface) return;
   const int s = d.fsolve[f];
@@ -108,7 +112,7 @@ __global__ void __launch_bounds__(128) k_flux(Dev d) {
   // ---- Eq. 4-14: the time-integrated flux in the face frame ----
   double Fn[4];
   gks::face_flux(WL, WR, SLn, SLt, SRn, SRt, WcL, WcR, idL, idR, mut_face, dt, fl.c_num, fl.pr_fix,
-                 [&](double lam) { return viscosity(fl, lam); }, Fn);
+                 [&](double h) { return viscosity_h(fl, h); }, Fn);
 
   // ---- back to the global frame, times the face length ----
   d.F[f] = Fn[0] * S;
@@ -119,8 +123,8 @@ __global__ void __launch_bounds__(128) k_flux(Dev d) {
   // ---- SA face terms (Eq. 28-30) and the coefficients of its implicit system ----
   double o4 = 0.0, o5 = 0.0, aLR = 0.0, aRL = 0.0, dgl = 0.0, dgr = 0.0;
   if (fl.sa_on) {
-    const double idn = 1.0 / d.fdn[f];
-    const double irl = 1.0 / WcLg[0], irr = 1.0 / WcRg[0];
+    const double idn = __drcp_rn(d.fdn[f]);
+    const double irl = __drcp_rn(WcLg[0]), irr = __drcp_rn(WcRg[0]);
     const double vni = (WcLg[1] * nx + WcLg[2] * ny) * irl;
     const double vnj = (WcRg[1] * nx + WcRg[2] * ny) * irr;
     const double nui = d.mu_l[L] * irl, nuj = muR * irr;

@@ -6,11 +6,16 @@
 // FP64 instructions:
 //  - every Maxwellian is set up with one reciprocal of the density and one reciprocal
 //    square root (1/(2 lambda) = 2 e / ((K+2) rho); sqrt(lambda) = rsqrt(2 / (2 lambda)));
-//  - a moment of a slope polynomial, <u^A v^B (a . psi) psi_k>, is assembled from the
-//    products U_a V_b of the tables and five-term dot products (mv below), instead of
-//    expanding every product psi_j psi_k;
-//  - the two half-space tables of the interface Maxwellian share one erfc and one exp,
-//    and e^(-dt/tau) is taken as 1 - (1 - e^(-dt/tau)) from the one expm1.
+//  - a moment of a slope polynomial, <u^A v^B (a . psi) psi_k>, is taken in the frame
+//    centred on the tangential velocity, where the odd moments of v - V vanish: the v and
+//    xi integrals reduce the slope to a quadratic in u, contracted with the u-table by
+//    three-term dot products (mv0 / mv1 below);
+//  - erfc(x) is taken as e^(-x^2) erfcx(x) (x >= 0) or 2 - e^(-x^2) erfcx(-x) (x < 0),
+//    with the e^(-lambda U^2) the first half-space moment needs anyway (erfcx costs two
+//    thirds of erfc on GB300); the two half-space tables of the interface Maxwellian share
+//    one erfcx and one exp; e^(-dt/tau) is taken as 1 - (1 - e^(-dt/tau)) from one expm1;
+//  - reciprocals are __drcp_rn (the correctly rounded 1/x, bitwise 1.0 / x, about a
+//    third cheaper than the division on GB300).
 #pragma once
 #include "igks_dev.h"
 
@@ -29,7 +34,7 @@ struct Maxw {
 __device__ __forceinline__ Maxw maxw_of(const double* W) {
   Maxw g;
   g.r = W[0];
-  const double ir = 1.0 / W[0];
+  const double ir = __drcp_rn(W[0]);
   g.U = W[1] * ir;
   g.V = W[2] * ir;
   const double e = W[3] - 0.5 * (W[1] * g.U + W[2] * g.V);    // internal energy per volume
@@ -54,22 +59,33 @@ __device__ __forceinline__ void table_rec(double U, double h, double* m) {
   for (int k = 0; k + 2 < N; k++) m[k + 2] = U * m[k + 1] + (k + 1) * h * m[k];
 }
 
+// erfc(x) / 2 from e2 = e^(-x^2): x >= 0 gives e2 erfcx(x) / 2, x < 0 gives
+// 1 - e2 erfcx(-x) / 2 (erfc(x) + erfc(-x) = 2)
+__device__ __forceinline__ double half_erfc(double x, double e2) {
+  const double t = 0.5 * e2 * erfcx(fabs(x));
+  return x >= 0.0 ? t : 1.0 - t;
+}
+
 // <u^n> over u >= 0 (sgn = +1) or u < 0 (sgn = -1):
 // <u^0> = erfc(-sgn sqrt(lambda) U) / 2, <u^1> = U <u^0> + sgn e^{-lambda U^2} / (2 sqrt(pi lambda))
 template <int N>
 __device__ __forceinline__ void table_half(const Maxw& g, double sgn, double* m) {
   const double isl = 2.0 * g.h * g.sl;   // 1/sqrt(lambda)
-  m[0] = 0.5 * erfc(-sgn * g.sl * g.U);
-  m[1] = g.U * m[0] + sgn * (0.5 * RSQRT_PI) * isl * exp(-g.lam * g.U * g.U);
+  const double x = g.sl * g.U;
+  const double e2 = exp(-x * x);
+  m[0] = half_erfc(-sgn * x, e2);
+  m[1] = g.U * m[0] + sgn * (0.5 * RSQRT_PI) * isl * e2;
   table_rec<N>(g.U, g.h, m);
 }
 
-// both half-space tables from one erfc and one exp: <u^0>_{u<0} = 1 - <u^0>_{u>=0}
+// both half-space tables from one erfcx and one exp: <u^0>_{u<0} = 1 - <u^0>_{u>=0}
 template <int N>
 __device__ __forceinline__ void table_half_pair(const Maxw& g, double* mp, double* mn) {
   const double isl = 2.0 * g.h * g.sl;
-  const double e = (0.5 * RSQRT_PI) * isl * exp(-g.lam * g.U * g.U);
-  mp[0] = 0.5 * erfc(-g.sl * g.U);
+  const double x = g.sl * g.U;
+  const double e2 = exp(-x * x);
+  const double e = (0.5 * RSQRT_PI) * isl * e2;
+  mp[0] = half_erfc(-x, e2);
   mn[0] = 1.0 - mp[0];
   mp[1] = g.U * mp[0] + e;
   mn[1] = g.U * mn[0] - e;
@@ -77,59 +93,87 @@ __device__ __forceinline__ void table_half_pair(const Maxw& g, double* mp, doubl
   table_rec<N>(g.U, g.h, mn);
 }
 
-// moments of the internal degrees of freedom: <xi^2> = K h, <xi^4> = K (K+2) h^2
-struct Xi {
-  double x1, x2;
+// The tangential velocity v is always integrated over the whole line, so the moments are
+// taken in the frame centred on it: v = V + c, where the odd moments of c vanish and
+// <c^2> = h, <c^4> = 3 h^2; the internal energy has <xi^2> = X1 = K h, <xi^4> = X2 =
+// K (K+2) h^2. Integrating c and xi out leaves polynomials of u, which are contracted with
+// the u-table (whole line or half line) of the Maxwellian.
+struct Frame {
+  double V, h, X1, K1, Vh, c1, c2;
+  // K1 = (h + X1 + V^2)/2, Vh = V^2 + h, c1 = h^2 + (X2 - X1^2)/2, c2 = (3h + X1 + V^2)/2
 };
-__device__ __forceinline__ Xi xi_of(double h) { return Xi{KDOF * h, KDOF * (KDOF + 2) * h * h}; }
-
-// <u^A v^B psi>, psi = (1, u, v, (u^2 + v^2 + xi^2)/2)
-template <int A, int B>
-__device__ __forceinline__ void mpsi(const double* u, const double* v, const Xi& x, double* o) {
-  const double p = u[A] * v[B];
-  o[0] = p;
-  o[1] = u[A + 1] * v[B];
-  o[2] = u[A] * v[B + 1];
-  o[3] = 0.5 * (u[A + 2] * v[B] + u[A] * v[B + 2] + x.x1 * p);
+__device__ __forceinline__ Frame frame_of(const Maxw& g) {
+  Frame f;
+  f.V = g.V;
+  f.h = g.h;
+  f.X1 = KDOF * g.h;
+  const double X2 = KDOF * (KDOF + 2) * g.h * g.h;
+  f.Vh = g.V * g.V + g.h;
+  f.K1 = 0.5 * (f.Vh + f.X1);
+  f.c1 = g.h * g.h + 0.5 * (X2 - f.X1 * f.X1);
+  f.c2 = 0.5 * (3.0 * g.h + f.X1 + g.V * g.V);
+  return f;
 }
 
-// slope polynomial a . psi = a0 + a1 u + a2 v + ha (u^2 + v^2 + xi^2), ha = a3 / 2
+// A slope polynomial a . psi = a0 + a1 u + a2 v + ha (u^2 + v^2 + xi^2), ha = a3/2, in the
+// centred frame: al0 + a1 u + al2 c + ha (u^2 + c^2 + xi^2) with al0 = a0 + a2 V + ha V^2,
+// al2 = a2 + 2 ha V. Integrated over c and xi it is S0(u) = s0 + a1 u + ha u^2 with
+// s0 = al0 + ha (h + X1); times c, c^2, c^3 or xi^2 (see mv0 / mv1) it gives multiples of
+// the same u-polynomial and of 1.
 struct Slope {
-  double a0, a1, a2, ha, c0, hx2;   // c0 = a0 + ha <xi^2>, hx2 = ha <xi^4>
+  double s0, a1, ha, a2h, ka, kb2, kb3;
+  // a2h = al2 h; ka = ha c1 + V al2 h (the u^0 term of the energy output, weight 1);
+  // kb2 = 2 (V al2 h + ha h^2), kb3 = al2 h c2 + 2 V ha h^2 (the same for the weight v)
 };
-__device__ __forceinline__ Slope slope_of(const double* a, const Xi& x) {
+__device__ __forceinline__ Slope slope_of(const double* a, const Frame& f) {
   Slope s;
-  s.a0 = a[0]; s.a1 = a[1]; s.a2 = a[2]; s.ha = 0.5 * a[3];
-  s.c0 = s.a0 + s.ha * x.x1;
-  s.hx2 = s.ha * x.x2;
+  s.ha = 0.5 * a[3];
+  s.a1 = a[1];
+  const double al0 = a[0] + f.V * (a[2] + s.ha * f.V);
+  const double al2 = a[2] + 2.0 * s.ha * f.V;
+  s.s0 = al0 + s.ha * (f.h + f.X1);
+  s.a2h = al2 * f.h;
+  const double hah2 = s.ha * f.h * f.h;
+  s.ka = s.ha * f.c1 + f.V * s.a2h;
+  s.kb2 = 2.0 * (f.V * s.a2h + hah2);
+  s.kb3 = s.a2h * f.c2 + 2.0 * f.V * hah2;
   return s;
 }
 
-// <u^I v^J (a . psi)> without the xi^2 part of the slope (t) and with it (returned)
-template <int I, int J>
-__device__ __forceinline__ double mq(const double* u, const double* v, const Slope& s, double* t) {
-  const double q = s.a1 * (u[I + 1] * v[J]) + s.a2 * (u[I] * v[J + 1]) + s.ha * (u[I + 2] * v[J] + u[I] * v[J + 2]);
-  const double p = u[I] * v[J];
-  if (t) *t = q + s.a0 * p;
-  return q + s.c0 * p;
+// P_j = <u^j S0(u)> over the u-table
+template <int J>
+__device__ __forceinline__ double pj(const double* u, const Slope& s) {
+  return s.s0 * u[J] + s.a1 * u[J + 1] + s.ha * u[J + 2];
 }
 
-// acc[k] += w * <u^A v^B (a . psi) psi_k>, k = 0..3
-template <int A, int B>
-__device__ __forceinline__ void mv(const double* u, const double* v, const Xi& x, const Slope& s, double w,
-                                   double* acc) {
-  double t;
-  const double r0 = mq<A, B>(u, v, s, &t);
-  const double r1 = mq<A + 1, B>(u, v, s, nullptr);
-  const double r2 = mq<A, B + 1>(u, v, s, nullptr);
-  // (u^2 + v^2 + xi^2)/2 times the slope: the u^2 and v^2 parts shift the table, the xi^2
-  // part multiplies the slope's own terms by <xi^2> and its xi^2 term by <xi^4>
-  const double r3 = 0.5 * (mq<A + 2, B>(u, v, s, nullptr) + mq<A, B + 2>(u, v, s, nullptr) + x.x1 * t +
-                           s.hx2 * (u[A] * v[B]));
-  acc[0] += w * r0;
-  acc[1] += w * r1;
-  acc[2] += w * r2;
-  acc[3] += w * r3;
+// acc[k] += w * <u^A (a . psi) psi_k>, psi = (1, u, v, (u^2 + v^2 + xi^2)/2)
+template <int A>
+__device__ __forceinline__ void mv0(const double* u, const Frame& f, const Slope& s, double w, double* acc) {
+  const double P0 = pj<A>(u, s), P1 = pj<A + 1>(u, s), P2 = pj<A + 2>(u, s);
+  acc[0] += w * P0;
+  acc[1] += w * P1;
+  acc[2] += w * (f.V * P0 + s.a2h * u[A]);
+  acc[3] += w * (0.5 * P2 + f.K1 * P0 + s.ka * u[A]);
+}
+
+// acc[k] += w * <u^A v (a . psi) psi_k>
+template <int A>
+__device__ __forceinline__ void mv1(const double* u, const Frame& f, const Slope& s, double w, double* acc) {
+  const double P0 = pj<A>(u, s), P1 = pj<A + 1>(u, s), P2 = pj<A + 2>(u, s);
+  const double r3 = 0.5 * P2 + f.K1 * P0 + s.ka * u[A];   // the energy output with weight 1
+  acc[0] += w * (f.V * P0 + s.a2h * u[A]);
+  acc[1] += w * (f.V * P1 + s.a2h * u[A + 1]);
+  acc[2] += w * (f.Vh * P0 + s.kb2 * u[A]);
+  acc[3] += w * (f.V * r3 + 0.5 * s.a2h * u[A + 2] + s.kb3 * u[A] + f.V * f.h * P0);
+}
+
+// <u^A psi> (no slope)
+template <int A>
+__device__ __forceinline__ void mpsi(const double* u, const Frame& f, double* o) {
+  o[0] = u[A];
+  o[1] = u[A + 1];
+  o[2] = f.V * u[A];
+  o[3] = 0.5 * u[A + 2] + f.K1 * u[A];
 }
 
 // Constants of the closed-form solve of <a psi>_g = b about one Maxwellian
@@ -169,51 +213,50 @@ struct SideSums {
 __device__ __forceinline__ double side_terms(const double* W, const double* sn, const double* st, double sgn,
                                              SideSums& acc) {
   const Maxw g = maxw_of(W);
-  const Xi x = xi_of(g.h);
-  double u[7], v[6];
+  const Frame fr = frame_of(g);
+  double u[7];
   table_full<7>(g.U, g.h, u);
-  table_full<6>(g.V, g.h, v);
   const MSolve ms = msolve_of(g);
   // slopes of Eq. 101 and the time slope of Eq. 11: <(a_n u + a_t v + A) psi>_g = 0
   double an[4], at[4], A[4], b[4];
-  const double ir = 1.0 / g.r;
+  const double ir = __drcp_rn(g.r);
 #pragma unroll
   for (int k = 0; k < 4; k++) b[k] = sn[k] * ir;
   solve(ms, b, an);
 #pragma unroll
   for (int k = 0; k < 4; k++) b[k] = st[k] * ir;
   solve(ms, b, at);
-  const Slope sn_ = slope_of(an, x), st_ = slope_of(at, x);
+  const Slope sn_ = slope_of(an, fr), st_ = slope_of(at, fr);
   double m[4] = {0, 0, 0, 0};
-  mv<1, 0>(u, v, x, sn_, 1.0, m);
-  mv<0, 1>(u, v, x, st_, 1.0, m);
+  mv0<1>(u, fr, sn_, 1.0, m);
+  mv1<0>(u, fr, st_, 1.0, m);
 #pragma unroll
   for (int k = 0; k < 4; k++) b[k] = -m[k];
   solve(ms, b, A);
-  const Slope sA = slope_of(A, x);
+  const Slope sA = slope_of(A, fr);
   // half-space moments of this side
   table_half<7>(g, sgn, u);
   double t[4];
-  mpsi<0, 0>(u, v, x, t);
+  mpsi<0>(u, fr, t);
 #pragma unroll
   for (int k = 0; k < 4; k++) acc.W0[k] += g.r * t[k];
-  mpsi<1, 0>(u, v, x, t);
+  mpsi<1>(u, fr, t);
 #pragma unroll
   for (int k = 0; k < 4; k++) acc.T3[k] += g.r * t[k];
-  mv<2, 0>(u, v, x, sn_, g.r, acc.T4);
-  mv<1, 1>(u, v, x, st_, g.r, acc.T4);
-  mv<1, 0>(u, v, x, sA, g.r, acc.T5);
-  mv<1, 0>(u, v, x, sn_, g.r, acc.S4);
-  mv<0, 1>(u, v, x, st_, g.r, acc.S4);
-  mv<0, 0>(u, v, x, sA, g.r, acc.S5);
+  mv0<2>(u, fr, sn_, g.r, acc.T4);
+  mv1<1>(u, fr, st_, g.r, acc.T4);
+  mv0<1>(u, fr, sA, g.r, acc.T5);
+  mv0<1>(u, fr, sn_, g.r, acc.S4);
+  mv1<0>(u, fr, st_, g.r, acc.S4);
+  mv0<0>(u, fr, sA, g.r, acc.S5);
   return g.r * g.h;   // p = rho / (2 lambda)
 }
 
 // The time-integrated flux of one face in the face frame (Eq. 13-14) with the Prandtl
 // fix. WL, WR: reconstructed face states; SLn.. their normal and tangential slopes;
 // WcL, WcR: the centre states of the two cells (rotated); idL, idR: reciprocal normal
-// distances centre to face; mu_face: laminar viscosity of the interface state is computed
-// here from the free-stream Sutherland law via visc(lambda0); mut: face eddy viscosity.
+// distances centre to face; visc(h0) gives the laminar viscosity of the interface state
+// from h0 = 1/(2 lambda0) (Sutherland's law); mut: face eddy viscosity.
 template <class Visc>
 __device__ __forceinline__ void face_flux(const double* WL, const double* WR, const double* SLn, const double* SLt,
                                           const double* SRn, const double* SRt, const double* WcL,
@@ -227,13 +270,12 @@ __device__ __forceinline__ void face_flux(const double* WL, const double* WR, co
 
   // interface equilibrium g0 (Eq. 5) and its slopes
   const Maxw g0 = maxw_of(acc.W0);
-  const Xi x = xi_of(g0.h);
-  double up[7], un[7], uf[7], v0[6];
+  const Frame fr = frame_of(g0);
+  double up[7], un[7], uf[7];
   table_full<7>(g0.U, g0.h, uf);
-  table_full<6>(g0.V, g0.h, v0);
   table_half_pair<7>(g0, up, un);
   const MSolve ms0 = msolve_of(g0);
-  const double ir0 = 1.0 / g0.r;
+  const double ir0 = __drcp_rn(g0.r);
   double abl[4], abr[4], abt[4], Ab[4];
   {
     double b[4];
@@ -248,23 +290,25 @@ __device__ __forceinline__ void face_flux(const double* WL, const double* WR, co
     for (int k = 0; k < 4; k++) b[k] = 0.5 * (SLt[k] + SRt[k]) * ir0;
     solve(ms0, b, abt);
   }
-  const Slope sl_ = slope_of(abl, x), sr_ = slope_of(abr, x), st_ = slope_of(abt, x);
+  const Slope sl_ = slope_of(abl, fr), sr_ = slope_of(abr, fr), st_ = slope_of(abt, fr);
   // Eq. 12 (reduced): <(abar_l u H + abar_r u (1-H) + abar_t v + Abar) psi>_g0 = 0
   double sq1[4] = {0, 0, 0, 0};
-  mv<1, 0>(up, v0, x, sl_, 1.0, sq1);
-  mv<1, 0>(un, v0, x, sr_, 1.0, sq1);
-  mv<0, 1>(uf, v0, x, st_, 1.0, sq1);
+  mv0<1>(up, fr, sl_, 1.0, sq1);
+  mv0<1>(un, fr, sr_, 1.0, sq1);
+  mv1<0>(uf, fr, st_, 1.0, sq1);
   {
     double b[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) b[k] = -sq1[k];
     solve(ms0, b, Ab);
   }
-  const Slope sA = slope_of(Ab, x);
+  const Slope sA = slope_of(Ab, fr);
 
   // collision time (Eq. 33-34 with the pressure-jump term) and the time weights of Eq. 13
-  const double p0 = g0.r * g0.h;
-  const double tau = (visc(g0.lam) + mut) / p0 + c_num * fabs(pL - pR) / (pL + pR) * dt;
+  // 1/p0 = 2 lambda0 / rho0 from the reciprocal already at hand
+  const double ip0 = 2.0 * g0.lam * ir0;
+  double tau = (visc(g0.h) + mut) * ip0;
+  if (c_num != 0.0) tau += c_num * fabs(pL - pR) / (pL + pR) * dt;
   const double xr = dt / tau;
   const double ome = -expm1(-xr);   // 1 - e^{-dt/tau}
   const double e = 1.0 - ome;
@@ -277,12 +321,12 @@ __device__ __forceinline__ void face_flux(const double* WL, const double* WR, co
 
   // Eq. 14, and the state integrals for the heat flux
   double t[4], eq1[4] = {0, 0, 0, 0}, eq2[4] = {0, 0, 0, 0}, sq2[4] = {0, 0, 0, 0};
-  mpsi<1, 0>(uf, v0, x, t);
-  mv<2, 0>(up, v0, x, sl_, 1.0, eq1);
-  mv<2, 0>(un, v0, x, sr_, 1.0, eq1);
-  mv<1, 1>(uf, v0, x, st_, 1.0, eq1);
-  mv<1, 0>(uf, v0, x, sA, 1.0, eq2);
-  mv<0, 0>(uf, v0, x, sA, 1.0, sq2);
+  mpsi<1>(uf, fr, t);
+  mv0<2>(up, fr, sl_, 1.0, eq1);
+  mv0<2>(un, fr, sr_, 1.0, eq1);
+  mv1<1>(uf, fr, st_, 1.0, eq1);
+  mv0<1>(uf, fr, sA, 1.0, eq2);
+  mv0<0>(uf, fr, sA, 1.0, sq2);
   double Ws[4];
 #pragma unroll
   for (int k = 0; k < 4; k++) {

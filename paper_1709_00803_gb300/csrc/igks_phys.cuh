@@ -20,6 +20,12 @@ __device__ __forceinline__ double viscosity(const DevFlow& fl, double lam) {
   return fl.mu_inf * tr * sqrt(tr) * (1.0 + fl.s_star) / (tr + fl.s_star);
 }
 
+// the same law from h = 1/(2 lambda): T/T_inf = 2 h lambda_inf, no division by lambda
+__device__ __forceinline__ double viscosity_h(const DevFlow& fl, double h) {
+  double tr = 2.0 * h * fl.lam_inf;
+  return fl.mu_inf * tr * sqrt(tr) * (1.0 + fl.s_star) / (tr + fl.s_star);
+}
+
 // eddy viscosity mu_t = rho nu_tilde fv1 (Eq. 34); zero for non-positive nu_tilde
 __device__ __forceinline__ double eddy_viscosity(const DevFlow& fl, double r, double nut, double mu) {
   if (!fl.sa_on || !(nut > 0.0)) return 0.0;
