@@ -262,7 +262,7 @@ def measure(args, mesh, flow, precision, dev, dist, ws, with_e2e):
     from paper_1709_00803_gb300 import igks
 
     stream = torch.cuda.Stream()
-    prec = igks.PREC_MIXED if precision == "mixed" else igks.PREC_FP64
+    prec = {"mixed": igks.PREC_MIXED, "df64": igks.PREC_DF64}.get(precision, igks.PREC_FP64)
     ctx = igks.Context(precision=prec, device=dev, stream=stream.cuda_stream, timing=1,
                        sweep_cluster=getattr(args, "sweep_cluster", 0))
     sid = ctx.mesh_upload(mesh)
@@ -338,7 +338,12 @@ def measure_batch(args, cases, precision, dev, dist, ws, with_e2e=False):
     ncells = np.array([m.n_cells for m, _ in cases])
     ctx.enqueue(args.warmup)
     stream.synchronize()
-    tuning = ctx.autotune(5)          # launch configuration for this batch (state restored)
+    if args.launch:                   # a given launch configuration instead of tuning
+        fb, stt, gr = (int(x) for x in args.launch.split(","))
+        tuning = dict(sweep_threads=stt, flux_block=fb, sweep_mode=1, sweep_cluster=1, groups=gr, ms_per_iter=0.0)
+        ctx.set_launch(tuning)
+    else:
+        tuning = ctx.autotune(5)      # launch configuration for this batch (state restored)
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     _, st = ctx.iterate(0)
     it0 = np.array([q["iters"] for q in st])
@@ -476,7 +481,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="igks", choices=["igks", "reference"])
-    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
+    ap.add_argument("--precision", default=None, choices=["fp64", "df64", "mixed"],
                     help="headline sweep precision (default: mixed for the batch, fp64 for one solve)")
     ap.add_argument("--workload", default="naca_batch", choices=list(WORKLOADS) + ["naca_batch", "serving", "cavity"])
     ap.add_argument("--explicit-cap", type=int, default=2000000, help="cavity: explicit iterations at most")
@@ -497,6 +502,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other", action="store_true", help="skip the other precision / the flat plate")
     ap.add_argument("--no-serving", action="store_true", help="batch: skip the bounded serving leg")
+    ap.add_argument("--launch", default="", help="batch: flux_block,sweep_threads,groups instead of autotune")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload == "naca_batch":
@@ -530,7 +536,8 @@ def main():
     out = {"metric": METRIC, "value": head["value"], "unit": METRIC, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if args.precision == "fp64" else "f64 flux/residual/update + f32 sweeps",
+           "dtype": {"fp64": "f64", "df64": "f64 flux/residual/update + double-float (2 x f32) sweeps"}.get(
+               args.precision, "f64 flux/residual/update + f32 sweeps"),
            "data": "synthetic",
            "config": {"workload": desc, "cells": mesh.n_cells, "faces": mesh.n_faces,
                       "sweep_levels": [head["info"]["levels_fwd"], head["info"]["levels_bwd"]],
@@ -662,7 +669,7 @@ def main_batch(args):
         # the turbulent flat plate, one solve, both sweep precisions
         mesh, flow = G.turbulent_plate(), F.turbulent_plate_flow()
         plate = {}
-        for prec in ("fp64", "mixed"):
+        for prec in ("fp64", "df64", "mixed"):
             r = measure(args, mesh, flow, prec, dev, dist, ws, with_e2e=False)
             plate[prec] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "kernel_ms": r["kernel_ms"],
                            "sweep_levels": list(r["levels"]), "clocks": r["clocks"]}

@@ -60,6 +60,8 @@ extern "C" {
 /* precision of the LU-SGS sweeps; flux, residual and state update are always FP64 */
 #define IGKS_PREC_FP64 0
 #define IGKS_PREC_MIXED 1   /* sweeps and implicit operator in FP32 */
+#define IGKS_PREC_DF64 2    /* sweeps in double-float (a pair of FP32 numbers, about 48 bits)
+                               on the FP32 pipes: FP64-grade increments at FP32 speed */
 
 #define IGKS_LIMITER_NONE 0
 #define IGKS_LIMITER_BJ 1      /* Barth-Jespersen reading of the min-max limiter, Eq. 9 */

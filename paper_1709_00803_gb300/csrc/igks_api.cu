@@ -624,7 +624,8 @@ int igks_create(const igks_options* opt, igks_ctx** out) {
   if (ctx->opt.check_every <= 0) ctx->opt.check_every = 20;
   if (ctx->opt.sweep_threads <= 0) ctx->opt.sweep_threads = NARROW_THREADS;
   if (ctx->opt.sweep_threads > NARROW_THREADS || ctx->opt.sweep_threads % 32) { delete ctx; return IGKS_EINVAL; }
-  if (ctx->opt.precision != IGKS_PREC_FP64 && ctx->opt.precision != IGKS_PREC_MIXED) { delete ctx; return IGKS_EINVAL; }
+  if (ctx->opt.precision != IGKS_PREC_FP64 && ctx->opt.precision != IGKS_PREC_MIXED &&
+      ctx->opt.precision != IGKS_PREC_DF64) { delete ctx; return IGKS_EINVAL; }
   if (ctx->opt.sweep_cluster <= 0) ctx->opt.sweep_cluster = 1;
   if (ctx->opt.groups <= 0) ctx->opt.groups = 1;
   if (ctx->opt.sweep_cluster != 1 && ctx->opt.sweep_cluster != 2 && ctx->opt.sweep_cluster != 4 &&
@@ -917,6 +918,13 @@ int igks_get_array(igks_ctx* ctx, int32_t solve, int32_t which, double* out) {
         CK(d2h_2d(ctx, tmp.data(), sizeof(float) * n, (const float*)src + ctx->cell_off[solve],
                   sizeof(float) * ctx->nc_pad, sizeof(float) * n, 5));
         for (size_t k = 0; k < tmp.size(); k++) out[k] = tmp[k];
+        return 0;
+      }
+      if (ctx->opt.precision == IGKS_PREC_DF64) {   // pairs (hi, lo) of floats
+        std::vector<float> tmp(10 * (size_t)n);
+        CK(d2h_2d(ctx, tmp.data(), 2 * sizeof(float) * n, (const float*)src + 2 * (size_t)ctx->cell_off[solve],
+                  2 * sizeof(float) * ctx->nc_pad, 2 * sizeof(float) * n, 5));
+        for (size_t k = 0; k < 5 * (size_t)n; k++) out[k] = (double)tmp[2 * k] + (double)tmp[2 * k + 1];
         return 0;
       }
       return get_cells(ctx, solve, (const double*)src, 5, out);

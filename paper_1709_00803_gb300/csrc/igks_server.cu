@@ -333,7 +333,8 @@ extern "C" {
 int igks_server_create(const igks_server_options* opt, igks_server** out) {
   if (!opt || !out) return IGKS_EINVAL;
   *out = nullptr;
-  if ((opt->precision != IGKS_PREC_FP64 && opt->precision != IGKS_PREC_MIXED) || opt->max_slots < 1 ||
+  if ((opt->precision != IGKS_PREC_FP64 && opt->precision != IGKS_PREC_MIXED && opt->precision != IGKS_PREC_DF64) ||
+      opt->max_slots < 1 ||
       opt->max_cohort < 1 || opt->iters_per_step < 1 || opt->max_iters < 1 || opt->hbm_budget < 0 ||
       !(opt->repack_fraction >= 0.0 && opt->repack_fraction <= 1.0))
     return IGKS_EINVAL;

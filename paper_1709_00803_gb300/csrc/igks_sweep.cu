@@ -21,6 +21,7 @@
 #include <cooperative_groups.h>
 #include <float.h>
 
+#include "igks_df64.cuh"
 #include "igks_dev.h"
 #include "igks_phys.cuh"
 
@@ -261,12 +262,12 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_update(Dev d) {
     double num = 0.0, den = 0.0;
 #pragma unroll
     for (int v = 0; v < 4; v++) {
-      const double dv = expl ? xf * d.M[v * n + i] : (double)dWo[v * n + i];
+      const double dv = expl ? xf * d.M[v * n + i] : to_double(dWo[v * n + i]);
       num += dv * dv;
       den += Wi[v] * Wi[v];
       Wi[v] += dv;
     }
-    Wi[4] += expl ? (d.flow[si].sa_on ? xf * d.M[4 * n + i] : 0.0) : (double)dWo[4 * n + i];
+    Wi[4] += expl ? (d.flow[si].sa_on ? xf * d.M[4 * n + i] : 0.0) : to_double(dWo[4 * n + i]);
     if (Wi[4] < 0.0) Wi[4] = 0.0;
     eq40 = sqrt(num) / sqrt(den);
     const double p = pressure_of(Wi[0], Wi[1], Wi[2], Wi[3]);
@@ -703,6 +704,7 @@ constexpr int WIDE_BLOCK = 128;
 
 void launch_update(const Dev& d, int precision, cudaStream_t s) {
   if (precision == 1) k_update<float><<<d.g_nblk, CELL_BLOCK, 0, s>>>(d);
+  else if (precision == 2) k_update<df64><<<d.g_nblk, CELL_BLOCK, 0, s>>>(d);
   else k_update<double><<<d.g_nblk, CELL_BLOCK, 0, s>>>(d);
 }
 
@@ -722,6 +724,7 @@ static void set_smem() {
 void setup_sweeps() {
   set_smem<double, 1>(); set_smem<double, 2>(); set_smem<double, 4>(); set_smem<double, 8>();
   set_smem<float, 1>(); set_smem<float, 2>(); set_smem<float, 4>(); set_smem<float, 8>();
+  set_smem<df64, 1>(); set_smem<df64, 2>(); set_smem<df64, 4>(); set_smem<df64, 8>();
 }
 
 // one block per solve (C = 1), or one cluster of C blocks per solve
@@ -760,6 +763,7 @@ static void launch_narrow_c(bool fwd, const Dev& d, int threads, cudaStream_t s)
 
 void launch_sweep_prep(const Dev& d, int precision, cudaStream_t s) {
   if (precision == 1) k_sweep_prep<float><<<d.g_nblk, CELL_BLOCK, 0, s>>>(d);
+  else if (precision == 2) k_sweep_prep<df64><<<d.g_nblk, CELL_BLOCK, 0, s>>>(d);
   else k_sweep_prep<double><<<d.g_nblk, CELL_BLOCK, 0, s>>>(d);
 }
 
@@ -769,11 +773,13 @@ void launch_sweep_fwd(const Dev& d, int precision, int threads, cudaStream_t s) 
       const int b = d.h_wfwd_ptr[l], e = d.h_wfwd_ptr[l + 1];
       const int g = (e - b + WIDE_BLOCK - 1) / WIDE_BLOCK;
       if (precision == 1) k_sweep_fwd_level<float><<<g, WIDE_BLOCK, 0, s>>>(d, b, e);
+      else if (precision == 2) k_sweep_fwd_level<df64><<<g, WIDE_BLOCK, 0, s>>>(d, b, e);
       else k_sweep_fwd_level<double><<<g, WIDE_BLOCK, 0, s>>>(d, b, e);
     }
     return;
   }
   if (precision == 1) launch_narrow_c<float>(true, d, threads, s);
+  else if (precision == 2) launch_narrow_c<df64>(true, d, threads, s);
   else launch_narrow_c<double>(true, d, threads, s);
 }
 
@@ -783,11 +789,13 @@ void launch_sweep_bwd(const Dev& d, int precision, int threads, cudaStream_t s) 
       const int b = d.h_wbwd_ptr[l], e = d.h_wbwd_ptr[l + 1];
       const int g = (e - b + WIDE_BLOCK - 1) / WIDE_BLOCK;
       if (precision == 1) k_sweep_bwd_level<float><<<g, WIDE_BLOCK, 0, s>>>(d, b, e);
+      else if (precision == 2) k_sweep_bwd_level<df64><<<g, WIDE_BLOCK, 0, s>>>(d, b, e);
       else k_sweep_bwd_level<double><<<g, WIDE_BLOCK, 0, s>>>(d, b, e);
     }
     return;
   }
   if (precision == 1) launch_narrow_c<float>(false, d, threads, s);
+  else if (precision == 2) launch_narrow_c<df64>(false, d, threads, s);
   else launch_narrow_c<double>(false, d, threads, s);
 }
 

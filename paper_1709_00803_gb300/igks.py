@@ -13,7 +13,7 @@ from . import build as _build
 
 OK, CONVERGED = 0, 1
 EINVAL, EMESH, ENOMEM, ECUDA, DIVERGED, TIMEOUT, EBUSY, MAXITER = -1, -2, -3, -4, -5, -6, -7, -8
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_DF64 = 0, 1, 2
 ARR = dict(grad=1, phi=2, lambda_f=3, lambda_c=4, flux=5, res=6, dwstar=7, dw=8, ghost=9,
            geom_cell=10, geom_face=11)
 

@@ -355,7 +355,7 @@ def test_refined_cavity_polygons_fp32_sweeps(permute):
     assert np.array_equal(out[0], out[1])
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_groups_of_solves_bitwise_equal_one_group(precision):
     """Solves split into groups that iterate on streams of their own (so one group's sweeps
     run beside another group's flux) do the same arithmetic: the fields are bitwise those of
@@ -404,3 +404,19 @@ def test_residual_history_matches_oracle_norms():
     assert np.array_equal(h[:, 0], ref[:, 0])
     assert np.all(np.abs(h[:, 1:] - ref[:, 1:]) <= 1e-10 * np.abs(ref[:, 1:]))
     assert len(ctx.get_history(sid, cap=7)) == 7 and ctx.get_history(sid, cap=7)[-1, 0] == 25
+
+
+@pytest.mark.parametrize("mk,flow_fn", [(G.laminar_plate, F.laminar_plate_flow),
+                                        (G.turbulent_plate, F.turbulent_plate_flow),
+                                        (lambda: G.refined_cavity(permute_seed=11), F.cavity_flow)])
+def test_double_float_sweeps_meet_the_fp64_bar(mk, flow_fn):
+    """Sweeps in double-float (pairs of FP32 numbers, about 48 bits, on the FP32 pipes):
+    one iteration compared term by term with the FP64 oracle at the FP64 bar (increments
+    within 1e-12 of max |W|, everything else 1e-12 relative), then 6 more iterations."""
+    m = mk()
+    fl = flow_fn()
+    ctx, sid, ora = make_pair(m, fl, seeded(m, fl, 51, amp=0.05), precision=2)
+    ctx.iterate(1); ora.iterate(1)
+    _compare_iteration(ctx, sid, ora)
+    ctx.iterate(6); ora.iterate(6)
+    assert_close("W after 7", ctx.get_fields(sid), ora.get(O.ORA_W), TOL)
