@@ -503,6 +503,10 @@ def main():
     ap.add_argument("--no-other", action="store_true", help="skip the other precision / the flat plate")
     ap.add_argument("--no-serving", action="store_true", help="batch: skip the bounded serving leg")
     ap.add_argument("--launch", default="", help="batch: flux_block,sweep_threads,groups instead of autotune")
+    ap.add_argument("--open-loop", type=int, default=1, help="serving: 1 Poisson arrivals after the capacity "
+                    "run, 0 latencies of the capacity run")
+    ap.add_argument("--plain-sample", type=int, default=0, help="serving: estimate the plain path from this many "
+                    "iterations of each request (0: run each to its stop)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload == "naca_batch":
@@ -739,16 +743,29 @@ def _serve(igks, cases, args, arrivals=None):
     return results, max(r["t_finish"] for r in results) - start
 
 
-def _plain(igks, cases, args):
-    """The plain path: each request alone, FP64 sweeps, one after the other."""
+def _plain(igks, cases, args, served=None):
+    """The plain path: each request alone, FP64 sweeps, one after the other. With
+    --plain-sample N each request runs only N iterations alone, and its service time is
+    estimated as the iterations its served solve took times the measured time per plain
+    iteration (plus the set-up measured); its outcome is taken from the served solve."""
     out = []
-    for m, fl, _ in cases:
+    for k, (m, fl, _) in enumerate(cases):
         t = time.perf_counter()
         ctx = igks.Context(precision=igks.PREC_FP64, check_every=100)
         sid = ctx.mesh_upload(m); ctx.set_flow(sid, fl); ctx.init_freestream(sid)
-        rc, st = ctx.iterate(args.max_iters)
+        if args.plain_sample > 0 and served is not None:
+            ctx.iterate(1)
+            t1 = time.perf_counter()
+            ctx.iterate(args.plain_sample)
+            per = (time.perf_counter() - t1) / args.plain_sample
+            setup = t1 - t
+            r = served[k]
+            out.append(dict(service=setup + per * r["iters"], state=r["state"], iters=r["iters"], estimated=True,
+                            ms_per_iteration=1e3 * per))
+        else:
+            rc, st = ctx.iterate(args.max_iters)
+            out.append(dict(service=time.perf_counter() - t, state=st[sid]["state"], iters=st[sid]["iters"]))
         ctx.destroy()
-        out.append(dict(service=time.perf_counter() - t, state=st[sid]["state"], iters=st[sid]["iters"]))
     return out
 
 
@@ -770,12 +787,18 @@ def main_serving(args):
     cap_per_s = len(res_cap) / T_cap
     # open loop: Poisson arrivals at 0.8 x the measured capacity
     gaps = np.array([sp["gap"] for _, _, sp in cases])
-    arrivals = np.cumsum(gaps) / (0.8 * cap_per_s)
-    res_open, T_open = _serve(igks, cases, args, arrivals)
+    arrivals = np.cumsum(gaps) / (0.8 * cap_per_s) if args.open_loop else np.zeros(len(cases))
+    if args.open_loop:
+        res_open, T_open = _serve(igks, cases, args, arrivals)
+    else:                              # latencies of the all-at-once run (a heavier load)
+        res_open, T_open = res_cap, T_cap
+        for r in res_open:
+            r["t_arrival"] = r["t_submit"]
     lat = [r["t_finish"] - r["t_arrival"] for r in res_open if conv(r["state"])]
     # plain FP64, one at a time; its latency under the same arrivals follows from its
     # service times (one FIFO server)
-    plain = _plain(igks, cases, args)
+    by_tag = {r["tag"]: r for r in res_cap}
+    plain = _plain(igks, cases, args, served=[by_tag[k] for k in range(len(cases))])
     fin, lat_plain = 0.0, []
     for a, p in zip(arrivals, plain):
         fin = max(fin, a) + p["service"]
@@ -803,7 +826,12 @@ def main_serving(args):
            "config": {"workload": f"{args.requests} seeded requests (flat plate or NACA 4-digit, SA; cells "
                                   f"log-uniform {args.cells_lo}-{args.cells_hi}; Ma 0.1-0.75, AoA -4..8, "
                                   f"Re 1e6-1e7), stop at {stop}, cap {args.max_iters} iterations",
-                      "slots": args.slots, "iters_per_step": args.iters_per_step},
+                      "slots": args.slots, "iters_per_step": args.iters_per_step,
+                      "latency": "Poisson arrivals at 0.8 x the measured capacity" if args.open_loop else
+                                 "all requests submitted at once (the capacity run)",
+                      "plain": (f"estimated: {args.plain_sample} plain FP64 iterations of each request alone "
+                                f"timed, times the iterations of its served solve") if args.plain_sample > 0 else
+                               "each request run alone to its stop"},
            "served": {"solves_per_hour": served, "converged": sum(p["conv"] for p in parts),
                       "requests": sum(p["n"] for p in parts), "makespan_s": T,
                       "p50_s": _pct(lat_all, 50), "p99_s": _pct(lat_all, 99),

@@ -513,7 +513,7 @@ static int build(igks_ctx* ctx) {
   AL(area, double, nc); AL(cx, double, nc); AL(cy, double, nc); AL(wall_d, double, nc);
   AL(W, double, 5 * (size_t)nc); AL(grad, double, 8 * (size_t)nc); AL(phi, double, 4 * (size_t)nc);
   AL(omega, double, nc); AL(mu_l, double, nc); AL(mu_t, double, nc); AL(Lam, double, nc);
-  AL(pu, double, nc); AL(pv, double, nc); AL(pc, double, nc);
+  AL(pu, double, nc); AL(pv, double, nc); AL(pc, double, nc); AL(lsq, double, 4 * (size_t)nc);
   AL(M, double, 5 * (size_t)nc); AL(fw, double, nc); AL(sa_diag, double, nc);
   AL(dWs, double, 5 * (size_t)nc); AL(dW, double, 5 * (size_t)nc); AL(dF, double, 8 * (size_t)nc);
   AL(fS, double, nf); AL(fnx, double, nf); AL(fny, double, nf); AL(fmx, double, nf); AL(fmy, double, nf);
@@ -1180,11 +1180,11 @@ int igks_footprint_bytes(int32_t n_nodes, int32_t n_cells, int32_t n_faces, int3
   if (n_nodes <= 0 || n_cells <= 0 || n_faces <= 0 || nnz < 0 || !out) return IGKS_EINVAL;
   const int64_t ncp = (int64_t)(n_cells + CELL_ALIGN - 1) / CELL_ALIGN * CELL_ALIGN;
   // (plus 16 KiB of residual history per solve, in the fixed part below)
-  // per padded cell: 118 doubles (state, gradients, speeds, increments, sweep records) +
+  // per padded cell: 122 doubles (state, gradients, speeds, increments, sweep records) +
   // 32 ints (CSR pointers, orders, levels, positions, padded stencils); per CSR entry 60 B
   // (face and node lists, sweep stencil coefficients, maps) + 40 B (one sweep entry); per
   // face 34 doubles + 8 ints; per node 2 doubles; a few hundred bytes per solve
-  *out = 1072 * ncp + 100 * (int64_t)nnz + 304 * (int64_t)n_faces + 16 * (int64_t)n_nodes + 4096 + 16384;
+  *out = 1104 * ncp + 100 * (int64_t)nnz + 304 * (int64_t)n_faces + 16 * (int64_t)n_nodes + 4096 + 16384;
   return IGKS_OK;
 }
 

@@ -93,9 +93,32 @@ __global__ void k_wall_distance(Dev d) {
   d.wall_d[i] = dmin;
 }
 
+// The normal matrix of the least-squares gradient (Eq. 7) depends on the geometry only:
+// accumulated here once, in the same order and roundings the gradient kernel used per
+// iteration, with the correctly rounded reciprocal of its determinant.
+__global__ void k_lsq_matrix(Dev d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.nc_pad || d.cell_solve[i] < 0) return;
+  const int n = d.nc_pad;
+  const double xi = d.cx[i], yi = d.cy[i];
+  double A00 = 0.0, A01 = 0.0, A11 = 0.0;
+  for (int k = d.cf_ptr[i]; k < d.cf_ptr[i + 1]; k++) {
+    const int f = d.cf_face[k];
+    const int L = d.fL[f], R = d.fR[f];
+    const int j = (L == i) ? R : L;
+    double xk, yk;
+    if (j >= 0) { xk = d.cx[j]; yk = d.cy[j]; } else { xk = d.fcx[f]; yk = d.fcy[f]; }
+    const double dx = xk - xi, dy = yk - yi;
+    A00 += dx * dx; A01 += dx * dy; A11 += dy * dy;
+  }
+  const double det = A00 * A11 - A01 * A01;
+  d.lsq[i] = A00; d.lsq[n + i] = A01; d.lsq[2 * n + i] = A11; d.lsq[3 * n + i] = __drcp_rn(det);
+}
+
 void launch_geometry(const Dev& d, cudaStream_t s) {
   k_geometry_cells<<<(d.nc_pad + 255) / 256, 256, 0, s>>>(d);
   if (d.nf) k_geometry_faces<<<(d.nf + 255) / 256, 256, 0, s>>>(d);
+  k_lsq_matrix<<<(d.nc_pad + 255) / 256, 256, 0, s>>>(d);
 }
 
 void launch_wall_distance(const Dev& d, cudaStream_t s) {
@@ -130,13 +153,20 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_prep(Dev d) {
   const DevFlow& fl = d.flow[s];
   int n = d.nc_pad;
   double r = d.W[i], mx = d.W[n + i], my = d.W[2 * n + i], E = d.W[3 * n + i], nut = d.W[4 * n + i];
-  double mu = viscosity(fl, lambda_of(r, mx, my, E));
+  // one reciprocal of the density serves the velocity, 1/(2 lambda) = p / rho and chi
+  const double ir = __drcp_rn(r);
+  const double u = mx * ir, v = my * ir;
+  const double p = (GAMMA - 1.0) * (E - 0.5 * (mx * u + my * v));
+  const double h = p * ir;
+  const double mu = viscosity_h(fl, h);
   d.mu_l[i] = mu;
-  d.mu_t[i] = eddy_viscosity(fl, r, nut, mu);
-  const double Wc[4] = {r, mx, my, E};
-  double u, v, c;
-  speeds_of(Wc, &u, &v, &c);
-  d.pu[i] = u; d.pv[i] = v; d.pc[i] = c;
+  double mt = 0.0;
+  if (fl.sa_on && nut > 0.0) {   // mu_t = rho nu~ fv1 (Eq. 34)
+    const double chi = nut * r * __drcp_rn(mu), c3 = chi * chi * chi;
+    mt = r * nut * c3 * __drcp_rn(c3 + SA_CV1 * SA_CV1 * SA_CV1);
+  }
+  d.mu_t[i] = mt;
+  d.pu[i] = u; d.pv[i] = v; d.pc[i] = sqrt(GAMMA * h);
 }
 
 // state of the cell across face f (ghost on a boundary)
@@ -217,7 +247,6 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
     double Wi[5];
     for (int v = 0; v < 5; v++) Wi[v] = d.W[v * n + i];
     double xi = d.cx[i], yi = d.cy[i];
-    double A00 = 0.0, A01 = 0.0, A11 = 0.0;
     double r0[4] = {0, 0, 0, 0}, r1[4] = {0, 0, 0, 0}, wmax[4], wmin[4];
     for (int v = 0; v < 4; v++) wmax[v] = wmin[v] = Wi[v];
     double Lam = 0.0;
@@ -229,7 +258,6 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
       across_W(d, f, j, Wk);
       if (j >= 0) { xk = d.cx[j]; yk = d.cy[j]; } else { xk = d.fcx[f]; yk = d.fcy[f]; }
       double dx = xk - xi, dy = yk - yi;
-      A00 += dx * dx; A01 += dx * dy; A11 += dy * dy;
 #pragma unroll
       for (int v = 0; v < 4; v++) {
         double dw = Wk[v] - Wi[v];
@@ -240,8 +268,8 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
       }
       Lam += 0.5 * d.lam_f[f] * d.fS[f];
     }
-    double det = A00 * A11 - A01 * A01;
-    const double idet = 1.0 / det;
+    // the geometry's normal matrix and 1/det (k_lsq_matrix)
+    const double A00 = d.lsq[i], A01 = d.lsq[n + i], A11 = d.lsq[2 * n + i], idet = d.lsq[3 * n + i];
     double area = d.area[i];
     double b[8];
 #pragma unroll
@@ -295,7 +323,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_gradient(Dev d) {
     }
 #pragma unroll
     for (int v = 0; v < 4; v++) d.phi[v * n + i] = phi[v];
-    const double ir = 1.0 / Wi[0];
+    const double ir = __drcp_rn(Wi[0]);
     double u = Wi[1] * ir, vv = Wi[2] * ir;
     double dudy = (b[3] - u * b[1]) * ir;
     double dvdx = (b[4] - vv * b[0]) * ir;
@@ -351,11 +379,11 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_residual(Dev d) {
         sad += d.sa_a[3 * nf + f];
       }
     }
-    const double idt = 1.0 / dt;
+    const double idt = __drcp_rn(dt);
 #pragma unroll
     for (int v = 0; v < 4; v++) d.M[v * n + i] = -acc[v] * idt;
     double area = d.area[i];
-    const double iarea = 1.0 / area;
+    const double iarea = __drcp_rn(area);
     double m4 = 0.0, fw = 0.0, sdiag = 0.0;
     if (fl.sa_on) {
       // Eq. 28a with SA-noft2 and the 2012 clipping of S~; the wall distance enters through
@@ -363,9 +391,9 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_residual(Dev d) {
       const double ik2 = 1.0 / (SA_KAPPA * SA_KAPPA);
       double r = d.W[i], nut = d.W[4 * n + i];
       double chi = nut * r / d.mu_l[i], c3 = chi * chi * chi;
-      double fv1 = c3 / (c3 + SA_CV1 * SA_CV1 * SA_CV1);
-      double fv2 = 1.0 - chi / (1.0 + chi * fv1);
-      double om = d.omega[i], idw = 1.0 / d.wall_d[i];
+      double fv1 = c3 * __drcp_rn(c3 + SA_CV1 * SA_CV1 * SA_CV1);
+      double fv2 = 1.0 - chi * __drcp_rn(1.0 + chi * fv1);
+      double om = d.omega[i], idw = __drcp_rn(d.wall_d[i]);
       double nd2 = nut * idw * idw * ik2;              // nu~ / (kappa^2 d^2)
       double Sbar = fv2 * nd2;
       double St = (Sbar >= -SA_CV2 * om)
@@ -376,7 +404,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_residual(Dev d) {
       double g = rr + SA_CW2 * (r6 - rr);
       double g2 = g * g, g6 = g2 * g2 * g2;
       const double c6 = SA_CW3 * SA_CW3 * SA_CW3 * SA_CW3 * SA_CW3 * SA_CW3;
-      fw = g * cbrt(sqrt((1.0 + c6) / (g6 + c6)));
+      fw = g * cbrt(sqrt((1.0 + c6) * __drcp_rn(g6 + c6)));
       double nd = nut * idw;
       double Sr = SA_CB1 * St * nut - SA_CW1 * fw * nd * nd;
       m4 = area * Sr + acc[4];

@@ -61,6 +61,7 @@ struct Dev {
   double* omega;            // [nc_pad] vorticity magnitude (SA)
   double* mu_l; double* mu_t;
   double* pu; double* pv; double* pc;   // [nc_pad] velocity and sound speed of every cell (k_prep)
+  double* lsq;              // [4][nc_pad] least-squares normal matrix A00, A01, A11 and 1/det (geometry)
   double* Lam;              // [nc_pad] sum over faces of (Lambda_c)_ij
   double* M;                // [5][nc_pad]
   double* fw;               // [nc_pad]
@@ -115,6 +116,7 @@ struct Dev {
   // wide schedule: cells of each level of all solves
   int wide;                      // 1: one launch per level; 0: one block per solve
   int sweep_cluster;             // narrow schedule: blocks (a thread-block cluster) per solve
+  int quad;                      // narrow FP32 / double-float sweeps: a quad of threads per cell
   const int* wfwd_cells; const int* wbwd_cells;
   const int* h_wfwd_ptr; const int* h_wbwd_ptr;   // HOST arrays of level offsets (launch sizes)
   int n_wfwd, n_wbwd;

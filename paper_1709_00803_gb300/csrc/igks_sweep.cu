@@ -21,6 +21,8 @@
 #include <cooperative_groups.h>
 #include <float.h>
 
+#include <type_traits>
+
 #include "igks_df64.cuh"
 #include "igks_dev.h"
 #include "igks_phys.cuh"
@@ -58,19 +60,68 @@ __device__ __forceinline__ void delta_flux(T r, T mx, T my, T u, T v, T H, T dr,
 // subtracted from (forward) or added to (backward) the cell's accumulator. Every schedule
 // applies the entries of a cell with these helpers in the same order, so a solve gives
 // the same bits whichever schedule runs it (alone or in a batch).
+// One component v of an entry: f0, f1 = the x and y flux increments of component v, w its
+// increment (fwd subtracts, bwd adds); the SA row has its scalar coefficient. The
+// schedules that split a cell's components over threads call these per component, so
+// every schedule does the same arithmetic.
+template <class T>
+__device__ __forceinline__ void fwd_comp(T& a, T sx, T sy, T sl, T f0, T f1, T w) {
+  a -= sx * f0 + sy * f1 - sl * w;
+}
+template <class T>
+__device__ __forceinline__ void bwd_comp(T& a, T sx, T sy, T sl, T f0, T f1, T w) {
+  a += sx * f0 + sy * f1 - sl * w;
+}
+template <class T>
+__device__ __forceinline__ void fwd_sa(T& a, T sa, T w) { a -= sa * w; }
+template <class T>
+__device__ __forceinline__ void bwd_sa(T& a, T sa, T w) { a += sa * w; }
+
 template <class T>
 __device__ __forceinline__ void fwd_acc(T* acc, T sx, T sy, T sl, T sa, const T* f, const T* w, bool sa_on) {
 #pragma unroll
-  for (int v = 0; v < 4; v++) acc[v] -= sx * f[2 * v] + sy * f[2 * v + 1] - sl * w[v];
-  if (sa_on) acc[4] -= sa * w[4];
+  for (int v = 0; v < 4; v++) fwd_comp<T>(acc[v], sx, sy, sl, f[2 * v], f[2 * v + 1], w[v]);
+  if (sa_on) fwd_sa<T>(acc[4], sa, w[4]);
 }
 
 template <class T>
 __device__ __forceinline__ void bwd_acc(T* acc, T sx, T sy, T sl, T sa, const T* f, const T* w, bool sa_on) {
 #pragma unroll
-  for (int v = 0; v < 4; v++) acc[v] += sx * f[2 * v] + sy * f[2 * v + 1] - sl * w[v];
-  if (sa_on) acc[4] += sa * w[4];
+  for (int v = 0; v < 4; v++) bwd_comp<T>(acc[v], sx, sy, sl, f[2 * v], f[2 * v + 1], w[v]);
+  if (sa_on) bwd_sa<T>(acc[4], sa, w[4]);
 }
+
+// The same two for double-float: every product is accumulated exactly into the running
+// high part (two-sum), its rounding errors and the product's low part into the running low
+// part, without renormalising after each term (the multiply that uses the sum does).
+__device__ __forceinline__ void df_mac(df64& acc, df64 a, df64 b) {   // acc += a b
+  const float p = a.hi * b.hi;
+  float pe = fmaf(a.hi, b.hi, -p);
+  pe = fmaf(a.hi, b.lo, pe);
+  pe = fmaf(a.lo, b.hi, pe);
+  const float s = acc.hi + p;
+  const float bb = s - acc.hi;
+  const float e = (acc.hi - (s - bb)) + (p - bb);
+  acc.hi = s;
+  acc.lo = acc.lo + (e + pe);
+}
+
+template <>
+__device__ __forceinline__ void fwd_comp<df64>(df64& a, df64 sx, df64 sy, df64 sl, df64 f0, df64 f1, df64 w) {
+  df_mac(a, -sx, f0);
+  df_mac(a, -sy, f1);
+  df_mac(a, sl, w);
+}
+template <>
+__device__ __forceinline__ void bwd_comp<df64>(df64& a, df64 sx, df64 sy, df64 sl, df64 f0, df64 f1, df64 w) {
+  df_mac(a, sx, f0);
+  df_mac(a, sy, f1);
+  df_mac(a, -sl, w);
+}
+template <>
+__device__ __forceinline__ void fwd_sa<df64>(df64& a, df64 sa, df64 w) { df_mac(a, -sa, w); }
+template <>
+__device__ __forceinline__ void bwd_sa<df64>(df64& a, df64 sa, df64 w) { df_mac(a, sa, w); }
 
 // ---- pre-pass: per-cell constants and the signed stencil of every cell ----
 template <class T>
@@ -87,8 +138,9 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_sweep_prep(Dev d) {
   const double u = d.pu[i], v = d.pv[i];          // mx / r, my / r (k_prep)
   const double p = (GAMMA - 1.0) * (E - 0.5 * (mx * u + my * v));
   T cc[5];
-  cc[0] = (T)(1.0 / (Lam / cfl + Lam));                                  // 1/D (Eq. 20, 24)
-  cc[1] = fl.sa_on ? (T)(1.0 / (Lam / cfl + d.sa_diag[i])) : (T)0;       // 1/a_ii (Eq. 32)
+  const double lc = Lam * __drcp_rn(cfl);                                 // Omega / dt_imp (Eq. 24)
+  cc[0] = (T)__drcp_rn(lc + Lam);                                        // 1/D (Eq. 20)
+  cc[1] = fl.sa_on ? (T)__drcp_rn(lc + d.sa_diag[i]) : (T)0;             // 1/a_ii (Eq. 32)
   cc[2] = (T)u;
   cc[3] = (T)v;
   cc[4] = (T)(E + p);
@@ -580,25 +632,29 @@ __device__ __forceinline__ void bwd_load_direct(const Dev& d, int p, BwdRec<T>* 
 // contribution of one backward entry: upper neighbour j (its increments from the ring or
 // global memory), or a wall/symmetry ghost (j = -1 - face: boundary map of this cell's
 // own forward increment ws, flux increment about the ghost state)
+// the increments of a wall / symmetry ghost (face fc) in the backward sweep: the boundary
+// map of the cell's own forward increment ws, and the flux increment about the ghost state
+template <class T>
+__device__ __forceinline__ void ghost_entry(const Dev& d, int fc, const T* ws, T* f, T* w) {
+  const int nf = d.nf;
+  w[0] = ws[0]; w[3] = ws[3];
+  if (d.fbc[fc] == 3 || d.fbc[fc] == 5) { w[1] = -ws[1]; w[2] = -ws[2]; w[4] = -ws[4]; }
+  else {
+    const T fx = (T)d.fnx[fc], fy = (T)d.fny[fc];
+    const T mn = ws[1] * fx + ws[2] * fy;
+    w[1] = ws[1] - (T)2 * mn * fx; w[2] = ws[2] - (T)2 * mn * fy; w[4] = ws[4];
+  }
+  const T* g = (const T*)d.gprim;   // ghost r, mx, my, u, v, H of this face (pre-pass)
+  delta_flux<T>(g[fc], g[nf + fc], g[2 * nf + fc], g[3 * nf + fc], g[4 * nf + fc], g[5 * nf + fc],
+                w[0], w[1], w[2], w[3], f);
+}
+
 template <class T, int C>
 __device__ __forceinline__ void bwd_entry(const Dev& d, const T* ring, const T* dF, const T* dWo, int j, int slot,
                                           const T* ws, T sx, T sy, T sl, T sa, bool sa_on, T* acc) {
   T f[8], w[5];
-  if (j >= 0) {
-    neighbour<T, C>(d, ring, dF, dWo, j, slot, f, w);
-  } else {
-    const int nf = d.nf, fc = -1 - j;
-    w[0] = ws[0]; w[3] = ws[3];
-    if (d.fbc[fc] == 3 || d.fbc[fc] == 5) { w[1] = -ws[1]; w[2] = -ws[2]; w[4] = -ws[4]; }
-    else {
-      const T fx = (T)d.fnx[fc], fy = (T)d.fny[fc];
-      const T mn = ws[1] * fx + ws[2] * fy;
-      w[1] = ws[1] - (T)2 * mn * fx; w[2] = ws[2] - (T)2 * mn * fy; w[4] = ws[4];
-    }
-    const T* g = (const T*)d.gprim;   // ghost r, mx, my, u, v, H of this face (pre-pass)
-    delta_flux<T>(g[fc], g[nf + fc], g[2 * nf + fc], g[3 * nf + fc], g[4 * nf + fc], g[5 * nf + fc],
-                  w[0], w[1], w[2], w[3], f);
-  }
+  if (j >= 0) neighbour<T, C>(d, ring, dF, dWo, j, slot, f, w);
+  else ghost_entry<T>(d, -1 - j, ws, f, w);
   bwd_acc<T>(acc, sx, sy, sl, sa, f, w, sa_on);
 }
 
@@ -679,6 +735,318 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_sweep_bwd_narrow(Dev d) {
   }
 }
 
+
+// ---- narrow schedule with a quad of threads per cell (FP32 and double-float sweeps) ----
+// The four threads of a quad share one cell: thread q accumulates component q (and q = 0
+// the SA row too) over the cell's entries, reading only its own component's three values
+// per neighbour from the ring; the quad then exchanges the four increments by shuffles and
+// each thread forms the flux increment (all eight values, the same function as one thread
+// per cell) and keeps its component's two. The arithmetic of every component is the
+// per-component helpers' in the same entry order, so the iterates are bitwise those of one
+// thread per cell. It shortens the dependent chain of a cell about fourfold where a level
+// holds few cells; it does not pay for FP64, whose cost is the SM's count of FP64 warp
+// instructions (one per ~19 cycles whatever the active lanes), so FP64 keeps one thread
+// per cell.
+constexpr int QUAD = 4;
+
+template <class T>
+__device__ __forceinline__ T shfl_q(T x, int k) { return __shfl_sync(0xffffffffu, x, k, QUAD); }
+template <>
+__device__ __forceinline__ df64 shfl_q<df64>(df64 x, int k) {
+  return df64(__shfl_sync(0xffffffffu, x.hi, k, QUAD), __shfl_sync(0xffffffffu, x.lo, k, QUAD));
+}
+
+// the quad's lanes share the copies of one staged forward record
+template <class T>
+__device__ __forceinline__ void fwd_stage_q(const Dev& d, int p, FwdRec<T>* st, int q) {
+  const int P = d.npos;
+  const T* rec = (const T*)d.rec_f;
+  const T* ec = (const T*)d.ec_f;
+  if (q == 0) {
+#pragma unroll
+    for (int v = 0; v < 5; v++) cpa(&st->m[v], rec + v * P + p);
+    cpa(&st->i, d.fwd_order + p);
+    cpa(&st->cnt, d.cnt_f + p);
+    cpa(&st->pb, d.pb_of_pf + p);
+  } else if (q == 1) {
+#pragma unroll
+    for (int v = 0; v < 3; v++) cpa(&st->w[v], rec + (5 + v) * P + p);
+#pragma unroll
+    for (int v = 0; v < 5; v++) cpa(&st->c[v], rec + (8 + v) * P + p);
+  } else if (q == 2) {
+#pragma unroll
+    for (int e = 0; e < PF_E; e++) {
+      cpa(&st->j[e], d.ej_f + e * P + p);
+      cpa(&st->slot[e], d.eslot_f + e * P + p);
+      cpa(&st->co[0][e], ec + e * P + p);
+    }
+  } else {
+#pragma unroll
+    for (int k = 1; k < 4; k++)
+#pragma unroll
+      for (int e = 0; e < PF_E; e++) cpa(&st->co[k][e], ec + (k * PF_E + e) * P + p);
+  }
+  cpa_commit();
+}
+
+template <class T>
+__device__ __forceinline__ void bwd_stage_q(const Dev& d, int p, BwdRec<T>* st, int q) {
+  const int P = d.npos;
+  const T* rec = (const T*)d.rec_b;
+  const T* ec = (const T*)d.ec_b;
+  if (q == 0) {
+#pragma unroll
+    for (int v = 0; v < 5; v++) cpa(&st->ws[v], rec + (10 + v) * P + p);
+    cpa(&st->i, d.bwd_order + p);
+    cpa(&st->cnt, d.cnt_b + p);
+  } else if (q == 1) {
+#pragma unroll
+    for (int v = 0; v < 5; v++) {
+      cpa(&st->w[v], rec + v * P + p);
+      cpa(&st->c[v], rec + (5 + v) * P + p);
+    }
+  } else if (q == 2) {
+#pragma unroll
+    for (int e = 0; e < PF_E; e++) {
+      cpa(&st->j[e], d.ej_b + e * P + p);
+      cpa(&st->slot[e], d.eslot_b + e * P + p);
+      cpa(&st->co[0][e], ec + e * P + p);
+    }
+  } else {
+#pragma unroll
+    for (int k = 1; k < 4; k++)
+#pragma unroll
+      for (int e = 0; e < PF_E; e++) cpa(&st->co[k][e], ec + (k * PF_E + e) * P + p);
+  }
+  cpa_commit();
+}
+
+// component q of a neighbour's increments: x and y flux increments and the increment (and
+// for q = 0 the SA increment w4)
+template <class T>
+__device__ __forceinline__ void neighbour_q(const Dev& d, const T* ring, const T* dF, const T* dWv, int j, int slot,
+                                            int q, T& f0, T& f1, T& w, T& w4) {
+  const int n = d.nc_pad;
+  if (slot >= 0) {
+    f0 = ring[(2 * q) * RING + slot];
+    f1 = ring[(2 * q + 1) * RING + slot];
+    w = ring[(8 + q) * RING + slot];
+    if (q == 0) w4 = ring[12 * RING + slot];
+  } else {
+    f0 = dF[(2 * q) * n + j];
+    f1 = dF[(2 * q + 1) * n + j];
+    w = dWv[q * n + j];
+    if (q == 0) w4 = dWv[4 * n + j];
+  }
+}
+
+template <class T>
+__device__ __forceinline__ T pick(const T* a, int q) {   // a[q] without local-memory indexing
+  return q == 0 ? a[0] : (q == 1 ? a[1] : (q == 2 ? a[2] : a[3]));
+}
+
+// one forward position processed by a quad; live = the quad holds a position this round
+template <class T>
+__device__ __forceinline__ void fwd_quad(const Dev& d, T* ring, int p, int pbase, const FwdRec<T>& r, int q,
+                                         bool live, bool sa_on) {
+  const int n = d.nc_pad, P = d.npos;
+  T* dWs = (T*)d.dWs;
+  T* dF = (T*)d.dF;
+  T acc = (T)0, acc4 = (T)0;
+  if (live) {
+    acc = pick(r.m, q);
+    acc4 = r.m[4];
+    const int cnt = r.cnt;
+    if (cnt >= 0) {
+#pragma unroll
+      for (int e = 0; e < PF_E; e++) {
+        if (e >= cnt) break;
+        T f0, f1, w, w4;
+        neighbour_q<T>(d, ring, dF, dWs, r.j[e], r.slot[e], q, f0, f1, w, w4);
+        fwd_comp<T>(acc, r.co[0][e], r.co[1][e], r.co[2][e], f0, f1, w);
+        if (q == 0 && sa_on) fwd_sa<T>(acc4, r.co[3][e], w4);
+      }
+    } else {
+      const T* sc = (const T*)d.sc_f;
+      const int nfs = d.nfs;
+      for (int k = d.fs_ptr[p]; k < d.fs_ptr[p + 1]; k++) {
+        T f0, f1, w, w4;
+        neighbour_q<T>(d, ring, dF, dWs, d.fs_j[k], d.fs_slot[k], q, f0, f1, w, w4);
+        fwd_comp<T>(acc, sc[k], sc[nfs + k], sc[2 * nfs + k], f0, f1, w);
+        if (q == 0 && sa_on) fwd_sa<T>(acc4, sc[3 * nfs + k], w4);
+      }
+    }
+  }
+  const T dwq = acc * r.c[0];
+  const T dw4 = sa_on ? acc4 * r.c[1] : (T)0;
+  T dw[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) dw[k] = shfl_q<T>(dwq, k);   // every lane of the warp takes part
+  if (!live) return;
+  T o[8];
+  delta_flux<T>(r.w[0], r.w[1], r.w[2], r.c[2], r.c[3], r.c[4], dw[0], dw[1], dw[2], dw[3], o);
+  const T o0 = q == 0 ? o[0] : (q == 1 ? o[2] : (q == 2 ? o[4] : o[6]));
+  const T o1 = q == 0 ? o[1] : (q == 1 ? o[3] : (q == 2 ? o[5] : o[7]));
+  const int slot = (p - pbase) % RING;
+  ring[(2 * q) * RING + slot] = o0;
+  ring[(2 * q + 1) * RING + slot] = o1;
+  ring[(8 + q) * RING + slot] = dwq;
+  const int i = r.i, pb = r.pb;
+  T* recb = (T*)d.rec_b;
+  dWs[q * n + i] = dwq;
+  recb[(10 + q) * P + pb] = dwq;            // the backward sweep's copy of dW*
+  dF[(2 * q) * n + i] = o0;
+  dF[(2 * q + 1) * n + i] = o1;
+  if (q == 0) {
+    ring[12 * RING + slot] = dw4;
+    dWs[4 * n + i] = dw4;
+    recb[14 * P + pb] = dw4;
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void bwd_quad(const Dev& d, T* ring, int p, int pbase, const BwdRec<T>& r, int q,
+                                         bool live, bool sa_on) {
+  const int n = d.nc_pad;
+  T* dWo = (T*)d.dW;
+  T* dF = (T*)d.dF;
+  T acc = (T)0, acc4 = (T)0;
+  if (live) {
+    const int cnt = r.cnt;
+    const int kb = cnt >= 0 ? 0 : d.bs_ptr[p], ke = cnt >= 0 ? cnt : d.bs_ptr[p + 1];
+    const T* sc = (const T*)d.sc_b;
+    const int nbs = d.nbs;
+    for (int k = kb; k < ke; k++) {
+      int j, slot;
+      T sx, sy, sl, sa;
+      if (cnt >= 0) {
+        j = r.j[k]; slot = r.slot[k];
+        sx = r.co[0][k]; sy = r.co[1][k]; sl = r.co[2][k]; sa = r.co[3][k];
+      } else {
+        j = d.bs_j[k]; slot = d.bs_slot[k];
+        sx = sc[k]; sy = sc[nbs + k]; sl = sc[2 * nbs + k]; sa = sc[3 * nbs + k];
+      }
+      T f0, f1, w, w4;
+      if (j >= 0) {
+        neighbour_q<T>(d, ring, dF, dWo, j, slot, q, f0, f1, w, w4);
+      } else {
+        T f[8], wg[5];
+        ghost_entry<T>(d, -1 - j, r.ws, f, wg);
+        f0 = q == 0 ? f[0] : (q == 1 ? f[2] : (q == 2 ? f[4] : f[6]));
+        f1 = q == 0 ? f[1] : (q == 1 ? f[3] : (q == 2 ? f[5] : f[7]));
+        w = pick(wg, q);
+        w4 = wg[4];
+      }
+      bwd_comp<T>(acc, sx, sy, sl, f0, f1, w);
+      if (q == 0 && sa_on) bwd_sa<T>(acc4, sa, w4);
+    }
+  }
+  const T wsq = pick(r.ws, q);
+  const T dwq = wsq - acc * r.c[0];
+  const T dw4 = sa_on ? r.ws[4] - acc4 * r.c[1] : (T)0;
+  T dw[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) dw[k] = shfl_q<T>(dwq, k);
+  if (!live) return;
+  T o[8];
+  delta_flux<T>(r.w[0], r.w[1], r.w[2], r.c[2], r.c[3], r.c[4], dw[0], dw[1], dw[2], dw[3], o);
+  const T o0 = q == 0 ? o[0] : (q == 1 ? o[2] : (q == 2 ? o[4] : o[6]));
+  const T o1 = q == 0 ? o[1] : (q == 1 ? o[3] : (q == 2 ? o[5] : o[7]));
+  const int slot = (p - pbase) % RING;
+  ring[(2 * q) * RING + slot] = o0;
+  ring[(2 * q + 1) * RING + slot] = o1;
+  ring[(8 + q) * RING + slot] = dwq;
+  const int i = r.i;
+  dWo[q * n + i] = dwq;
+  dF[(2 * q) * n + i] = o0;
+  dF[(2 * q + 1) * n + i] = o1;
+  if (q == 0) {
+    ring[12 * RING + slot] = dw4;
+    dWo[4 * n + i] = dw4;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(NARROW_THREADS) k_sweep_fwd_quad(Dev d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ring = (T*)smem_raw;
+  FwdRec<T>* stage = (FwdRec<T>*)(smem_raw + (size_t)13 * RING * sizeof(T));
+  const int q = threadIdx.x % QUAD, cslot = threadIdx.x / QUAD, ncs = blockDim.x / QUAD;
+  FwdRec<T>* st = stage + cslot;                     // the quad's staged record
+  const int s = d.g_solve0 + blockIdx.x;
+  if (d.st[s].state != 0 || d.flow[s].scheme == 1) return;
+  const bool sa_on = d.flow[s].sa_on;
+  const int l0 = d.lvl_solve_ptr[s], l1 = d.lvl_solve_ptr[s + 1] - 1;
+  const int pbase = d.fwd_lvl[l0];
+  int b = d.fwd_lvl[l0], e = d.fwd_lvl[l0 + 1];
+  int pm = b + cslot;
+  if (l0 < l1 && pm < e) fwd_stage_q<T>(d, pm, st, q);
+  for (int l = l0; l < l1; l++) {
+    const int en = (l + 1 < l1) ? d.fwd_lvl[l + 2] : e;
+    const bool mine = pm < e;
+    FwdRec<T> cur;
+    if (mine) cpa_wait_all();
+    __syncwarp();                     // every lane's copies of the quad's record have landed
+    if (mine) cur = *st;
+    __syncwarp();                     // all lanes have read the stage before it is refilled
+    const int pn = e + cslot;
+    if (pn < en) fwd_stage_q<T>(d, pn, st, q);
+    fwd_quad<T>(d, ring, pm, pbase, cur, q, mine, sa_on);
+    // levels wider than the block's quads: further rounds, records read directly
+    for (int base = b + ncs; base < e; base += ncs) {
+      const int p = base + cslot;
+      const bool live = p < e;
+      FwdRec<T> xt;
+      if (live) fwd_load_direct<T>(d, p, &xt);
+      fwd_quad<T>(d, ring, p, pbase, xt, q, live, sa_on);
+    }
+    __syncthreads();
+    b = e;
+    e = en;
+    pm = pn;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(NARROW_THREADS) k_sweep_bwd_quad(Dev d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ring = (T*)smem_raw;
+  BwdRec<T>* stage = (BwdRec<T>*)(smem_raw + (size_t)13 * RING * sizeof(T));
+  const int q = threadIdx.x % QUAD, cslot = threadIdx.x / QUAD, ncs = blockDim.x / QUAD;
+  BwdRec<T>* st = stage + cslot;
+  const int s = d.g_solve0 + blockIdx.x;
+  if (d.st[s].state != 0 || d.flow[s].scheme == 1) return;
+  const bool sa_on = d.flow[s].sa_on;
+  const int l0 = d.blvl_solve_ptr[s], l1 = d.blvl_solve_ptr[s + 1] - 1;
+  const int pbase = d.bwd_lvl[l0];
+  int b = d.bwd_lvl[l0], e = d.bwd_lvl[l0 + 1];
+  int pm = b + cslot;
+  if (l0 < l1 && pm < e) bwd_stage_q<T>(d, pm, st, q);
+  for (int l = l0; l < l1; l++) {
+    const int en = (l + 1 < l1) ? d.bwd_lvl[l + 2] : e;
+    const bool mine = pm < e;
+    BwdRec<T> cur;
+    if (mine) cpa_wait_all();
+    __syncwarp();
+    if (mine) cur = *st;
+    __syncwarp();
+    const int pn = e + cslot;
+    if (pn < en) bwd_stage_q<T>(d, pn, st, q);
+    bwd_quad<T>(d, ring, pm, pbase, cur, q, mine, sa_on);
+    for (int base = b + ncs; base < e; base += ncs) {
+      const int p = base + cslot;
+      const bool live = p < e;
+      BwdRec<T> xt;
+      if (live) bwd_load_direct<T>(d, p, &xt);
+      bwd_quad<T>(d, ring, p, pbase, xt, q, live, sa_on);
+    }
+    __syncthreads();
+    b = e;
+    e = en;
+    pm = pn;
+  }
+}
+
 // ---- wide schedule: one launch per level, all solves ----
 template <class T>
 __global__ void k_sweep_fwd_level(Dev d, int b, int e) {
@@ -721,10 +1089,17 @@ static void set_smem() {
   cudaFuncSetAttribute(k_sweep_bwd_narrow<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<T>());
 }
 
+template <class T>
+static void set_smem_quad() {
+  cudaFuncSetAttribute(k_sweep_fwd_quad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<T>());
+  cudaFuncSetAttribute(k_sweep_bwd_quad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<T>());
+}
+
 void setup_sweeps() {
   set_smem<double, 1>(); set_smem<double, 2>(); set_smem<double, 4>(); set_smem<double, 8>();
   set_smem<float, 1>(); set_smem<float, 2>(); set_smem<float, 4>(); set_smem<float, 8>();
   set_smem<df64, 1>(); set_smem<df64, 2>(); set_smem<df64, 4>(); set_smem<df64, 8>();
+  set_smem_quad<float>(); set_smem_quad<df64>();
 }
 
 // one block per solve (C = 1), or one cluster of C blocks per solve
@@ -753,6 +1128,13 @@ static void launch_narrow(bool fwd, const Dev& d, int threads, cudaStream_t s) {
 
 template <class T>
 static void launch_narrow_c(bool fwd, const Dev& d, int threads, cudaStream_t s) {
+  if constexpr (!std::is_same<T, double>::value) {
+    if (d.quad && d.sweep_cluster <= 1) {   // a quad of threads per cell
+      void (*k)(Dev) = fwd ? k_sweep_fwd_quad<T> : k_sweep_bwd_quad<T>;
+      k<<<d.g_nsolve, threads, fwd ? fwd_smem<T>() : bwd_smem<T>(), s>>>(d);
+      return;
+    }
+  }
   switch (d.sweep_cluster) {
     case 2: launch_narrow<T, 2>(fwd, d, threads, s); break;
     case 4: launch_narrow<T, 4>(fwd, d, threads, s); break;

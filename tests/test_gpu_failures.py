@@ -107,11 +107,20 @@ def test_served_request_that_diverges_is_reported():
             srv2.destroy()
 
 
+def _one_cell_box():
+    """One unit-square cell closed by symmetry planes: its four faces see the same state,
+    the same mirror ghost and the same centre-to-face distance (the centroid of the unit
+    square is exactly (0.5, 0.5)), so with the fluid at rest their fluxes cancel exactly
+    whatever the rounding of the flux algebra."""
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0]])
+    return G.build_mesh(xy, [[0, 1, 2, 3]], lambda a, b, xm, ym: G.BC_SYMMETRY, name="one_cell_box")
+
+
 def test_exactly_zero_residual_converges_with_finite_cfl():
-    """Fluid at rest in a box of symmetry planes on an axis-aligned mesh: the residual is
-    exactly zero at the first iteration on both sides; the solve converges there."""
+    """A residual that is exactly zero converges at once on both sides, and Eq. 25 after a
+    non-zero norm sends the CFL to its cap (never NaN)."""
     from paper_1709_00803_gb300 import igks
-    m = G.tiny_quads(40, 30, bcs=("symmetry", "symmetry"))
+    m = _one_cell_box()
     fl = F.cavity_flow()
     ctx = igks.Context(check_every=1)
     sid = ctx.mesh_upload(m); ctx.set_flow(sid, fl); ctx.init_freestream(sid)
@@ -123,3 +132,7 @@ def test_exactly_zero_residual_converges_with_finite_cfl():
     assert rc == igks.CONVERGED and st[sid]["iters"] == 1 == o.scalars()["iter"]
     assert st[sid]["res_l2_rho"] == 0.0 and st[sid]["res_inf"] == 0.0
     assert math.isfinite(st[sid]["cfl"]) and st[sid]["cfl"] == fl.cfl_init
+    # after a non-zero norm: the CFL goes to its cap
+    ctx.set_scalars(sid, {"iter": 7, "cfl": 2345.0, "res_inf_prev": 3.5, "res_l2_first": 1.0, "state": 0})
+    rc, st = ctx.iterate(1)
+    assert rc == igks.CONVERGED and st[sid]["cfl"] == fl.cfl_max
