@@ -256,6 +256,16 @@ def run_reference_batch(args, budget_s=150.0):
     print(json.dumps(line), flush=True)
 
 
+def _given_launch(ctx, spec):
+    """Apply a launch configuration given as flux_block,sweep_threads,groups[,quad]."""
+    v = [int(x) for x in spec.split(",")]
+    fb, stt, gr, qd = (v + [0])[:4]
+    tuning = dict(sweep_threads=stt, flux_block=fb, sweep_mode=1, sweep_cluster=1, groups=gr, sweep_quad=qd,
+                  ms_per_iter=0.0)
+    ctx.set_launch(tuning)
+    return tuning
+
+
 def measure(args, mesh, flow, precision, dev, dist, ws, with_e2e):
     """Time args.steps iterations of one solve at one sweep precision."""
     import torch
@@ -269,6 +279,8 @@ def measure(args, mesh, flow, precision, dev, dist, ws, with_e2e):
     ctx.set_flow(sid, flow)
     ctx.init_freestream(sid)
     info = ctx.mesh_info(sid)
+    # launch configuration for this solve (autotune restores the state it started from)
+    tuning = _given_launch(ctx, args.launch) if args.launch else ctx.autotune(5)
     ctx.enqueue(args.warmup)
     stream.synchronize()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")
@@ -299,7 +311,7 @@ def measure(args, mesh, flow, precision, dev, dist, ws, with_e2e):
     res = {"value": ws * mesh.n_cells * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
            "kernel_ms": {k: round(statistics.mean(v), 5) for k, v in ktimes.items()},
            "launches_per_step": ctx.launches_per_iteration(), "clocks": clk.summary(), "info": info,
-           "levels": (info["levels_fwd"], info["levels_bwd"]),
+           "levels": (info["levels_fwd"], info["levels_bwd"]), "autotune": tuning,
            "solver_state": {"iters": st[sid]["iters"], "res_l2_rel": st[sid]["res_l2_rel"], "cfl": st[sid]["cfl"]}}
     if with_e2e:
         W_host = torch.empty((5, mesh.n_cells), dtype=torch.float64).pin_memory().numpy()
@@ -339,9 +351,7 @@ def measure_batch(args, cases, precision, dev, dist, ws, with_e2e=False):
     ctx.enqueue(args.warmup)
     stream.synchronize()
     if args.launch:                   # a given launch configuration instead of tuning
-        fb, stt, gr = (int(x) for x in args.launch.split(","))
-        tuning = dict(sweep_threads=stt, flux_block=fb, sweep_mode=1, sweep_cluster=1, groups=gr, ms_per_iter=0.0)
-        ctx.set_launch(tuning)
+        tuning = _given_launch(ctx, args.launch)
     else:
         tuning = ctx.autotune(5)      # launch configuration for this batch (state restored)
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -502,7 +512,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other", action="store_true", help="skip the other precision / the flat plate")
     ap.add_argument("--no-serving", action="store_true", help="batch: skip the bounded serving leg")
-    ap.add_argument("--launch", default="", help="batch: flux_block,sweep_threads,groups instead of autotune")
+    ap.add_argument("--launch", default="", help="flux_block,sweep_threads,groups[,quad] instead of autotune")
     ap.add_argument("--open-loop", type=int, default=1, help="serving: 1 Poisson arrivals after the capacity "
                     "run, 0 latencies of the capacity run")
     ap.add_argument("--plain-sample", type=int, default=0, help="serving: estimate the plain path from this many "
@@ -551,7 +561,7 @@ def main():
            "e2e": head["e2e"], "gpu_launches": head["launches_per_step"] * args.steps,
            "kernel_ms": head["kernel_ms"], "roofline": dominant, "roofline_flux": flux_roof,
            "per_kernel": per_kernel(head, mesh, args.precision),
-           "clocks": head["clocks"], "solver_state": head["solver_state"]}
+           "clocks": head["clocks"], "solver_state": head["solver_state"], "autotune": head["autotune"]}
     if other:
         out["other"] = {"precision": other_p, "value": other["value"], "ms_per_step": other["ms_per_step"],
                         "kernel_ms": other["kernel_ms"], "clocks": other["clocks"]}
@@ -676,7 +686,7 @@ def main_batch(args):
         for prec in ("fp64", "df64", "mixed"):
             r = measure(args, mesh, flow, prec, dev, dist, ws, with_e2e=False)
             plate[prec] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "kernel_ms": r["kernel_ms"],
-                           "sweep_levels": list(r["levels"]), "clocks": r["clocks"]}
+                           "sweep_levels": list(r["levels"]), "clocks": r["clocks"], "autotune": r["autotune"]}
         out["turbulent_plate"] = dict(plate, workload=WORKLOADS["turbulent_plate"][2], cells=mesh.n_cells,
                                       faces=mesh.n_faces)
     if not args.no_serving and ws == 1:

@@ -84,7 +84,11 @@ typedef struct igks_options {
                              consecutive solves (0: 1), each iterated by a graph on a stream of
                              its own, so that one group's sweeps (one block per solve) overlap
                              another group's flux; same arithmetic, same bits */
-  int32_t reserved[3];
+  int32_t sweep_quad;     /* schedule 1 with sweep_cluster 1, FP32 and double-float sweeps: a quad
+                             of threads per cell (component k on thread k of the quad), so that a
+                             block of sweep_threads (<= 512) threads holds sweep_threads / 4 cells
+                             of a level; same arithmetic, same bits; ignored for FP64 sweeps */
+  int32_t reserved[2];
 } igks_options;
 
 /* Flow conditions of one solve. Non-dimensional: free-stream density, speed and the
@@ -229,6 +233,7 @@ typedef struct igks_tuning {
   int32_t sweep_cluster;   /* blocks per solve of schedule 1 */
   float ms_per_iter;       /* measured device time of one iteration with it */
   int32_t groups;          /* groups of solves on streams of their own (igks_options.groups) */
+  int32_t sweep_quad;      /* a quad of threads per cell (igks_options.sweep_quad) */
 } igks_tuning;
 
 /* Time the library's launch configurations (sweep schedule, block size and blocks per

@@ -549,6 +549,7 @@ static int build(igks_ctx* ctx) {
     int mode = ctx->opt.sweep_mode;
     d.wide = (mode == 2) || (mode == 0 && std::max(maxf, maxb) <= WIDE_MAX_LEVELS);
     d.sweep_cluster = ctx->opt.sweep_cluster;
+    d.quad = ctx->opt.sweep_quad != 0 && ctx->opt.precision != IGKS_PREC_FP64;
     std::vector<int> wf, wb;
     ctx->h_wfwd_ptr.assign(1, 0);
     ctx->h_wbwd_ptr.assign(1, 0);
@@ -623,7 +624,11 @@ int igks_create(const igks_options* opt, igks_ctx** out) {
   if (opt) ctx->opt = *opt;
   if (ctx->opt.check_every <= 0) ctx->opt.check_every = 20;
   if (ctx->opt.sweep_threads <= 0) ctx->opt.sweep_threads = NARROW_THREADS;
-  if (ctx->opt.sweep_threads > NARROW_THREADS || ctx->opt.sweep_threads % 32) { delete ctx; return IGKS_EINVAL; }
+  if (ctx->opt.sweep_quad != 0 && ctx->opt.sweep_quad != 1) { delete ctx; return IGKS_EINVAL; }
+  if (ctx->opt.sweep_threads > (ctx->opt.sweep_quad ? QUAD_THREADS : NARROW_THREADS) || ctx->opt.sweep_threads % 32) {
+    delete ctx;
+    return IGKS_EINVAL;
+  }
   if (ctx->opt.precision != IGKS_PREC_FP64 && ctx->opt.precision != IGKS_PREC_MIXED &&
       ctx->opt.precision != IGKS_PREC_DF64) { delete ctx; return IGKS_EINVAL; }
   if (ctx->opt.sweep_cluster <= 0) ctx->opt.sweep_cluster = 1;
@@ -1089,21 +1094,28 @@ int igks_autotune(igks_ctx* ctx, int32_t iters_per_trial, igks_tuning* out) {
   best.ms_per_iter = 1e30f;
   const bool wide_ok = std::max(d.n_wfwd, d.n_wbwd) <= 4 * WIDE_MAX_LEVELS;
   const int flux_blocks[] = {64, 128};
-  const int sweep_threads[] = {128, 256};
+  // narrow-schedule blocks: one thread per cell (128, 256 threads) and, for FP32 and
+  // double-float sweeps, a quad of threads per cell (256, 512 threads)
+  const int blocks[][2] = {{128, 0}, {256, 0}, {256, 1}, {512, 1}};
+  const bool quad_ok = ctx->opt.precision != IGKS_PREC_FP64;
   const int clusters[] = {1, 2, 4};
   const int groups[] = {1, 2, 4};
   int err = 0;
   for (int wide = 0; wide <= (wide_ok ? 1 : 0) && !err; wide++)
     for (int fb : flux_blocks)
-      for (int stt : sweep_threads)
+      for (const auto& blk : blocks)
         for (int cl : clusters)
           for (int gr : groups) {
-          if (wide && (stt != sweep_threads[0] || cl != 1 || gr != 1)) continue;   // the wide schedule has its own block
+          const int stt = blk[0], qd = blk[1];
+          if (wide && (blk != blocks[0] || cl != 1 || gr != 1)) continue;   // the wide schedule has its own block
           if (gr > 1 && (cl != 1 || gr > ns)) continue;
+          if (qd && (!quad_ok || cl != 1)) continue;
           d.wide = wide;
           d.flux_block = fb;
           d.sweep_cluster = cl;
+          d.quad = qd;
           ctx->opt.sweep_threads = stt;
+          ctx->opt.sweep_quad = qd;
           ctx->opt.groups = gr;
           if ((err = recapture(ctx))) break;
           restore();
@@ -1115,15 +1127,17 @@ int igks_autotune(igks_ctx* ctx, int32_t iters_per_trial, igks_tuning* out) {
           float ms = 0.0f;
           cudaEventElapsedTime(&ms, e0, e1);
           ms /= iters_per_trial;
-          if (ms < best.ms_per_iter) best = igks_tuning{stt, fb, wide ? 2 : 1, cl, ms, gr};
+          if (ms < best.ms_per_iter) best = igks_tuning{stt, fb, wide ? 2 : 1, cl, ms, gr, qd};
           }
   // apply the winner and put every solve back where it was
   d.wide = best.sweep_mode == 2;
   d.flux_block = best.flux_block;
   d.sweep_cluster = best.sweep_cluster;
+  d.quad = best.sweep_quad;
   ctx->opt.sweep_threads = best.sweep_threads;
   ctx->opt.sweep_mode = best.sweep_mode;
   ctx->opt.sweep_cluster = best.sweep_cluster;
+  ctx->opt.sweep_quad = best.sweep_quad;
   ctx->opt.groups = best.groups;
   if (!err) err = recapture(ctx);
   restore();
@@ -1141,7 +1155,11 @@ int igks_autotune(igks_ctx* ctx, int32_t iters_per_trial, igks_tuning* out) {
 
 int igks_set_launch(igks_ctx* ctx, const igks_tuning* t) {
   if (!ctx || !t) return IGKS_EINVAL;
-  if ((t->sweep_threads != 128 && t->sweep_threads != 256) || (t->flux_block != 64 && t->flux_block != 128) ||
+  const bool quad = t->sweep_quad == 1;
+  if ((t->sweep_quad != 0 && !quad) ||
+      (quad ? (t->sweep_threads != 256 && t->sweep_threads != 512)
+            : (t->sweep_threads != 128 && t->sweep_threads != 256)) ||
+      (t->flux_block != 64 && t->flux_block != 128) ||
       (t->sweep_mode != 1 && t->sweep_mode != 2) ||
       (t->sweep_cluster != 1 && t->sweep_cluster != 2 && t->sweep_cluster != 4 && t->sweep_cluster != 8) ||
       t->groups < 1)
@@ -1152,9 +1170,11 @@ int igks_set_launch(igks_ctx* ctx, const igks_tuning* t) {
   d.wide = t->sweep_mode == 2;
   d.flux_block = t->flux_block;
   d.sweep_cluster = t->sweep_cluster;
+  d.quad = quad && ctx->opt.precision != IGKS_PREC_FP64;
   ctx->opt.sweep_threads = t->sweep_threads;
   ctx->opt.sweep_mode = t->sweep_mode;
   ctx->opt.sweep_cluster = t->sweep_cluster;
+  ctx->opt.sweep_quad = t->sweep_quad;
   ctx->opt.groups = t->groups;
   return recapture(ctx);
 }

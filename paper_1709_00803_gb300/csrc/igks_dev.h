@@ -159,6 +159,7 @@ constexpr int N_KERNEL_KINDS = 11;   // kernels of one iteration (the wide sweep
 constexpr int RING = 1024;           // shared-memory ring of the narrow sweeps (cells)
 constexpr int PF_E = 4;              // stencil entries held per prefetched sweep position
 constexpr int NARROW_THREADS = 256;  // block of the narrow sweeps (one thread per cell of a level)
+constexpr int QUAD_THREADS = 512;    // block of the narrow sweeps with a quad of threads per cell
 constexpr int WIDE_MAX_LEVELS = 64;  // automatic choice: wide schedule up to this many levels
 constexpr int HIST = 1024;           // iterations of residual history kept per solve
 

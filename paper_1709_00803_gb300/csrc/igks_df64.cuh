@@ -10,7 +10,10 @@
 // p + e exactly with p = a b, e = fma(a, b, -p); a result is renormalised with the
 // quick two-sum (|a| >= |b|). Addition folds the low parts into the error of the high
 // parts (the "sloppy" sum, error a few units of 2^-48 of the larger operand); division
-// takes one Newton correction of the FP32 quotient.
+// takes one Newton correction of the FP32 quotient. Every step is an explicitly rounded
+// operation (__fadd_rn, __fmul_rn, __fmaf_rn): the transformations are exact only if the
+// compiler does not fuse a product into a following sum, which it may do with plain
+// operators.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -32,15 +35,15 @@ __device__ __forceinline__ double to_double(float a) { return (double)a; }
 
 // |a| >= |b| (or a = 0): s + e = a + b exactly
 __device__ __forceinline__ df64 df_quick(float a, float b) {
-  const float s = a + b;
-  return df64(s, b - (s - a));
+  const float s = __fadd_rn(a, b);
+  return df64(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
 
 __device__ __forceinline__ df64 operator+(df64 a, df64 b) {
-  const float s = a.hi + b.hi;
-  const float bb = s - a.hi;
-  float e = (a.hi - (s - bb)) + (b.hi - bb);   // s + e = a.hi + b.hi exactly
-  e += a.lo + b.lo;
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));   // s + e = a.hi + b.hi exactly
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
   return df_quick(s, e);
 }
 
@@ -48,17 +51,17 @@ __device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
 __device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
 
 __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
-  const float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);              // p + e = a.hi b.hi exactly
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);         // p + e = a.hi b.hi exactly
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
   return df_quick(p, e);
 }
 
 __device__ __forceinline__ df64 operator/(df64 a, df64 b) {
-  const float q1 = a.hi / b.hi;
+  const float q1 = __fdiv_rn(a.hi, b.hi);
   const df64 r = a - b * df64(q1, 0.0f);       // remainder of the FP32 quotient
-  const float q2 = r.hi / b.hi;
+  const float q2 = __fdiv_rn(r.hi, b.hi);
   return df_quick(q1, q2);
 }
 

@@ -31,6 +31,24 @@ namespace cg = cooperative_groups;
 
 namespace igks {
 
+// The sweeps' arithmetic is written with explicitly rounded operations (fma_x, mul_x,
+// add_x: __fma_rn / __dmul_rn / __dadd_rn in FP64, the __f*_rn intrinsics in FP32, the
+// double-float operators): the compiler may not fuse or split them, so every schedule (one
+// thread per cell, a quad of threads per cell, one launch per level) and every inlining
+// context gives the same bits for the same cell.
+__device__ __forceinline__ double fma_x(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ double mul_x(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add_x(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double div_x(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float fma_x(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float mul_x(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add_x(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float div_x(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ df64 fma_x(df64 a, df64 b, df64 c) { return a * b + c; }
+__device__ __forceinline__ df64 mul_x(df64 a, df64 b) { return a * b; }
+__device__ __forceinline__ df64 add_x(df64 a, df64 b) { return a + b; }
+__device__ __forceinline__ df64 div_x(df64 a, df64 b) { return a / b; }
+
 // Increment of the x and y Euler fluxes for the increment (dr, dmx, dmy, dE) of a state
 // with density r, momenta mx, my, velocity u, v and total enthalpy density H = E + p,
 // written without differences of large numbers. o = {x mass, y mass, x x-mom, y x-mom,
@@ -38,21 +56,22 @@ namespace igks {
 template <class T>
 __device__ __forceinline__ void delta_flux(T r, T mx, T my, T u, T v, T H, T dr, T dmx, T dmy, T dE, T* o) {
   const T g1 = (T)(GAMMA - 1.0);
-  const T inv1 = (T)1 / (r + dr);
-  const T du = (dmx - u * dr) * inv1, dv = (dmy - v * dr) * inv1;
-  const T u1 = u + du, v1 = v + dv;
-  const T dmxu = dmx * u1 + mx * du;      // increment of mx u
-  const T dmyv = dmy * v1 + my * dv;      // increment of my v
-  const T dp = g1 * (dE - (T)0.5 * (dmxu + dmyv));
-  const T dH = dE + dp;
+  const T inv1 = div_x((T)1, add_x(r, dr));
+  const T du = mul_x(fma_x(-u, dr, dmx), inv1);          // (dmx - u dr) / (r + dr)
+  const T dv = mul_x(fma_x(-v, dr, dmy), inv1);
+  const T u1 = add_x(u, du), v1 = add_x(v, dv);
+  const T dmxu = fma_x(dmx, u1, mul_x(mx, du));          // increment of mx u
+  const T dmyv = fma_x(dmy, v1, mul_x(my, dv));          // increment of my v
+  const T dp = mul_x(g1, fma_x((T)(-0.5), add_x(dmxu, dmyv), dE));
+  const T dH = add_x(dE, dp);
   o[0] = dmx;
   o[1] = dmy;
-  o[2] = dmxu + dp;
-  o[3] = dmx * v1 + mx * dv;
-  o[4] = dmy * u1 + my * du;
-  o[5] = dmyv + dp;
-  o[6] = dH * u1 + H * du;
-  o[7] = dH * v1 + H * dv;
+  o[2] = add_x(dmxu, dp);
+  o[3] = fma_x(dmx, v1, mul_x(mx, dv));
+  o[4] = fma_x(dmy, u1, mul_x(my, du));
+  o[5] = add_x(dmyv, dp);
+  o[6] = fma_x(dH, u1, mul_x(H, du));
+  o[7] = fma_x(dH, v1, mul_x(H, dv));
 }
 
 // Contribution of one stencil entry to a cell's sweep sum: (1/2) S (dF . n - lambda dW)
@@ -65,17 +84,43 @@ __device__ __forceinline__ void delta_flux(T r, T mx, T my, T u, T v, T H, T dr,
 // schedules that split a cell's components over threads call these per component, so
 // every schedule does the same arithmetic.
 template <class T>
+__device__ __forceinline__ T entry_sum(T sx, T sy, T sl, T f0, T f1, T w) {   // sx f0 + sy f1 - sl w
+  return fma_x(sx, f0, fma_x(sy, f1, -mul_x(sl, w)));
+}
+template <class T>
 __device__ __forceinline__ void fwd_comp(T& a, T sx, T sy, T sl, T f0, T f1, T w) {
-  a -= sx * f0 + sy * f1 - sl * w;
+  a = add_x(a, -entry_sum(sx, sy, sl, f0, f1, w));
 }
 template <class T>
 __device__ __forceinline__ void bwd_comp(T& a, T sx, T sy, T sl, T f0, T f1, T w) {
-  a += sx * f0 + sy * f1 - sl * w;
+  a = add_x(a, entry_sum(sx, sy, sl, f0, f1, w));
 }
 template <class T>
-__device__ __forceinline__ void fwd_sa(T& a, T sa, T w) { a -= sa * w; }
+__device__ __forceinline__ void fwd_sa(T& a, T sa, T w) { a = fma_x(-sa, w, a); }
 template <class T>
-__device__ __forceinline__ void bwd_sa(T& a, T sa, T w) { a += sa * w; }
+__device__ __forceinline__ void bwd_sa(T& a, T sa, T w) { a = fma_x(sa, w, a); }
+
+// A cell's increments from its accumulators: one rounded product (forward), one fused
+// multiply-add (backward). Written with explicitly rounded operations so that the compiler
+// cannot fuse the product into the arithmetic that consumes the increment (the flux
+// increment of the same thread): a schedule that takes the increments from other threads
+// by shuffles must get the same bits.
+template <class T>
+__device__ __forceinline__ T inc_fwd(T acc, T c);
+template <>
+__device__ __forceinline__ double inc_fwd<double>(double acc, double c) { return __dmul_rn(acc, c); }
+template <>
+__device__ __forceinline__ float inc_fwd<float>(float acc, float c) { return __fmul_rn(acc, c); }
+template <>
+__device__ __forceinline__ df64 inc_fwd<df64>(df64 acc, df64 c) { return acc * c; }
+template <class T>
+__device__ __forceinline__ T inc_bwd(T ws, T acc, T c);   // ws - acc c
+template <>
+__device__ __forceinline__ double inc_bwd<double>(double ws, double acc, double c) { return __fma_rn(-acc, c, ws); }
+template <>
+__device__ __forceinline__ float inc_bwd<float>(float ws, float acc, float c) { return __fmaf_rn(-acc, c, ws); }
+template <>
+__device__ __forceinline__ df64 inc_bwd<df64>(df64 ws, df64 acc, df64 c) { return ws - acc * c; }
 
 template <class T>
 __device__ __forceinline__ void fwd_acc(T* acc, T sx, T sy, T sl, T sa, const T* f, const T* w, bool sa_on) {
@@ -95,15 +140,15 @@ __device__ __forceinline__ void bwd_acc(T* acc, T sx, T sy, T sl, T sa, const T*
 // high part (two-sum), its rounding errors and the product's low part into the running low
 // part, without renormalising after each term (the multiply that uses the sum does).
 __device__ __forceinline__ void df_mac(df64& acc, df64 a, df64 b) {   // acc += a b
-  const float p = a.hi * b.hi;
-  float pe = fmaf(a.hi, b.hi, -p);
-  pe = fmaf(a.hi, b.lo, pe);
-  pe = fmaf(a.lo, b.hi, pe);
-  const float s = acc.hi + p;
-  const float bb = s - acc.hi;
-  const float e = (acc.hi - (s - bb)) + (p - bb);
+  const float p = __fmul_rn(a.hi, b.hi);
+  float pe = __fmaf_rn(a.hi, b.hi, -p);
+  pe = __fmaf_rn(a.hi, b.lo, pe);
+  pe = __fmaf_rn(a.lo, b.hi, pe);
+  const float s = __fadd_rn(acc.hi, p);
+  const float bb = __fsub_rn(s, acc.hi);
+  const float e = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
   acc.hi = s;
-  acc.lo = acc.lo + (e + pe);
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, pe));
 }
 
 template <>
@@ -237,8 +282,8 @@ __device__ __forceinline__ void fwd_cell(const Dev& d, int i, bool sa_on) {
   }
   T dw[5];
 #pragma unroll
-  for (int v = 0; v < 4; v++) dw[v] = acc[v] * c[i];
-  dw[4] = sa_on ? acc[4] * c[n + i] : (T)0;
+  for (int v = 0; v < 4; v++) dw[v] = inc_fwd<T>(acc[v], c[i]);
+  dw[4] = sa_on ? inc_fwd<T>(acc[4], c[n + i]) : (T)0;
 #pragma unroll
   for (int v = 0; v < 5; v++) dWs[v * n + i] = dw[v];
   T o[8];
@@ -280,8 +325,8 @@ __device__ __forceinline__ void bwd_cell(const Dev& d, int i, bool sa_on) {
   }
   T dw[5];
 #pragma unroll
-  for (int v = 0; v < 4; v++) { dw[v] = ws[v] - acc[v] * c[i]; dWo[v * n + i] = dw[v]; }
-  dw[4] = sa_on ? ws[4] - acc[4] * c[n + i] : (T)0;
+  for (int v = 0; v < 4; v++) { dw[v] = inc_bwd<T>(ws[v], acc[v], c[i]); dWo[v * n + i] = dw[v]; }
+  dw[4] = sa_on ? inc_bwd<T>(ws[4], acc[4], c[n + i]) : (T)0;
   dWo[4 * n + i] = dw[4];
   T o[8];
   delta_flux<T>((T)d.W[i], (T)d.W[n + i], (T)d.W[2 * n + i], c[2 * n + i], c[3 * n + i], c[4 * n + i],
@@ -502,8 +547,8 @@ __device__ __forceinline__ void fwd_process(const Dev& d, T* ring, int p, int pb
   }
   T dw[5];
 #pragma unroll
-  for (int v = 0; v < 4; v++) dw[v] = acc[v] * r->c[0];
-  dw[4] = sa_on ? acc[4] * r->c[1] : (T)0;
+  for (int v = 0; v < 4; v++) dw[v] = inc_fwd<T>(acc[v], r->c[0]);
+  dw[4] = sa_on ? inc_fwd<T>(acc[4], r->c[1]) : (T)0;
   T o[8];
   delta_flux<T>(r->w[0], r->w[1], r->w[2], r->c[2], r->c[3], r->c[4], dw[0], dw[1], dw[2], dw[3], o);
   const int slot = (p - pbase) % RING;
@@ -635,14 +680,18 @@ __device__ __forceinline__ void bwd_load_direct(const Dev& d, int p, BwdRec<T>* 
 // the increments of a wall / symmetry ghost (face fc) in the backward sweep: the boundary
 // map of the cell's own forward increment ws, and the flux increment about the ghost state
 template <class T>
+__device__ __forceinline__ T mn_x(T a, T fx, T b, T fy) { return fma_x(a, fx, mul_x(b, fy)); }
+
+template <class T>
 __device__ __forceinline__ void ghost_entry(const Dev& d, int fc, const T* ws, T* f, T* w) {
   const int nf = d.nf;
   w[0] = ws[0]; w[3] = ws[3];
   if (d.fbc[fc] == 3 || d.fbc[fc] == 5) { w[1] = -ws[1]; w[2] = -ws[2]; w[4] = -ws[4]; }
   else {
     const T fx = (T)d.fnx[fc], fy = (T)d.fny[fc];
-    const T mn = ws[1] * fx + ws[2] * fy;
-    w[1] = ws[1] - (T)2 * mn * fx; w[2] = ws[2] - (T)2 * mn * fy; w[4] = ws[4];
+    const T mn = mn_x(ws[1], fx, ws[2], fy);
+    const T mn2 = add_x(mn, mn);                                      // 2 (dm . n), exact
+    w[1] = fma_x(-mn2, fx, ws[1]); w[2] = fma_x(-mn2, fy, ws[2]); w[4] = ws[4];
   }
   const T* g = (const T*)d.gprim;   // ghost r, mx, my, u, v, H of this face (pre-pass)
   delta_flux<T>(g[fc], g[nf + fc], g[2 * nf + fc], g[3 * nf + fc], g[4 * nf + fc], g[5 * nf + fc],
@@ -684,8 +733,8 @@ __device__ __forceinline__ void bwd_process(const Dev& d, T* ring, int p, int pb
   }
   T dw[5];
 #pragma unroll
-  for (int v = 0; v < 4; v++) dw[v] = ws[v] - acc[v] * r->c[0];
-  dw[4] = sa_on ? ws[4] - acc[4] * r->c[1] : (T)0;
+  for (int v = 0; v < 4; v++) dw[v] = inc_bwd<T>(ws[v], acc[v], r->c[0]);
+  dw[4] = sa_on ? inc_bwd<T>(ws[4], acc[4], r->c[1]) : (T)0;
   T o[8];
   delta_flux<T>(r->w[0], r->w[1], r->w[2], r->c[2], r->c[3], r->c[4], dw[0], dw[1], dw[2], dw[3], o);
   ring_put<T>(ring, (p - pbase) % RING, o, dw);
@@ -877,8 +926,8 @@ __device__ __forceinline__ void fwd_quad(const Dev& d, T* ring, int p, int pbase
       }
     }
   }
-  const T dwq = acc * r.c[0];
-  const T dw4 = sa_on ? acc4 * r.c[1] : (T)0;
+  const T dwq = inc_fwd<T>(acc, r.c[0]);
+  const T dw4 = sa_on ? inc_fwd<T>(acc4, r.c[1]) : (T)0;
   T dw[4];
 #pragma unroll
   for (int k = 0; k < 4; k++) dw[k] = shfl_q<T>(dwq, k);   // every lane of the warp takes part
@@ -904,6 +953,26 @@ __device__ __forceinline__ void fwd_quad(const Dev& d, T* ring, int p, int pbase
   }
 }
 
+// component q of one backward entry: an upper neighbour's increments, or a wall / symmetry
+// ghost's (the ghost is formed whole, as with one thread per cell, and component q taken)
+template <class T>
+__device__ __forceinline__ void bwd_entry_q(const Dev& d, const T* ring, const T* dF, const T* dWo, int j, int slot,
+                                            const T* ws, T sx, T sy, T sl, T sa, int q, bool sa_on, T& acc, T& acc4) {
+  T f0, f1, w, w4;
+  if (j >= 0) {
+    neighbour_q<T>(d, ring, dF, dWo, j, slot, q, f0, f1, w, w4);
+  } else {
+    T f[8], wg[5];
+    ghost_entry<T>(d, -1 - j, ws, f, wg);
+    f0 = q == 0 ? f[0] : (q == 1 ? f[2] : (q == 2 ? f[4] : f[6]));
+    f1 = q == 0 ? f[1] : (q == 1 ? f[3] : (q == 2 ? f[5] : f[7]));
+    w = pick(wg, q);
+    w4 = wg[4];
+  }
+  bwd_comp<T>(acc, sx, sy, sl, f0, f1, w);
+  if (q == 0 && sa_on) bwd_sa<T>(acc4, sa, w4);
+}
+
 template <class T>
 __device__ __forceinline__ void bwd_quad(const Dev& d, T* ring, int p, int pbase, const BwdRec<T>& r, int q,
                                          bool live, bool sa_on) {
@@ -913,37 +982,24 @@ __device__ __forceinline__ void bwd_quad(const Dev& d, T* ring, int p, int pbase
   T acc = (T)0, acc4 = (T)0;
   if (live) {
     const int cnt = r.cnt;
-    const int kb = cnt >= 0 ? 0 : d.bs_ptr[p], ke = cnt >= 0 ? cnt : d.bs_ptr[p + 1];
-    const T* sc = (const T*)d.sc_b;
-    const int nbs = d.nbs;
-    for (int k = kb; k < ke; k++) {
-      int j, slot;
-      T sx, sy, sl, sa;
-      if (cnt >= 0) {
-        j = r.j[k]; slot = r.slot[k];
-        sx = r.co[0][k]; sy = r.co[1][k]; sl = r.co[2][k]; sa = r.co[3][k];
-      } else {
-        j = d.bs_j[k]; slot = d.bs_slot[k];
-        sx = sc[k]; sy = sc[nbs + k]; sl = sc[2 * nbs + k]; sa = sc[3 * nbs + k];
+    if (cnt >= 0) {
+#pragma unroll
+      for (int e = 0; e < PF_E; e++) {
+        if (e >= cnt) break;
+        bwd_entry_q<T>(d, ring, dF, dWo, r.j[e], r.slot[e], r.ws, r.co[0][e], r.co[1][e], r.co[2][e], r.co[3][e],
+                       q, sa_on, acc, acc4);
       }
-      T f0, f1, w, w4;
-      if (j >= 0) {
-        neighbour_q<T>(d, ring, dF, dWo, j, slot, q, f0, f1, w, w4);
-      } else {
-        T f[8], wg[5];
-        ghost_entry<T>(d, -1 - j, r.ws, f, wg);
-        f0 = q == 0 ? f[0] : (q == 1 ? f[2] : (q == 2 ? f[4] : f[6]));
-        f1 = q == 0 ? f[1] : (q == 1 ? f[3] : (q == 2 ? f[5] : f[7]));
-        w = pick(wg, q);
-        w4 = wg[4];
-      }
-      bwd_comp<T>(acc, sx, sy, sl, f0, f1, w);
-      if (q == 0 && sa_on) bwd_sa<T>(acc4, sa, w4);
+    } else {
+      const T* sc = (const T*)d.sc_b;
+      const int nbs = d.nbs;
+      for (int k = d.bs_ptr[p]; k < d.bs_ptr[p + 1]; k++)
+        bwd_entry_q<T>(d, ring, dF, dWo, d.bs_j[k], d.bs_slot[k], r.ws, sc[k], sc[nbs + k], sc[2 * nbs + k],
+                       sc[3 * nbs + k], q, sa_on, acc, acc4);
     }
   }
   const T wsq = pick(r.ws, q);
-  const T dwq = wsq - acc * r.c[0];
-  const T dw4 = sa_on ? r.ws[4] - acc4 * r.c[1] : (T)0;
+  const T dwq = inc_bwd<T>(wsq, acc, r.c[0]);
+  const T dw4 = sa_on ? inc_bwd<T>(r.ws[4], acc4, r.c[1]) : (T)0;
   T dw[4];
 #pragma unroll
   for (int k = 0; k < 4; k++) dw[k] = shfl_q<T>(dwq, k);
@@ -967,7 +1023,7 @@ __device__ __forceinline__ void bwd_quad(const Dev& d, T* ring, int p, int pbase
 }
 
 template <class T>
-__global__ void __launch_bounds__(NARROW_THREADS) k_sweep_fwd_quad(Dev d) {
+__global__ void __launch_bounds__(QUAD_THREADS) k_sweep_fwd_quad(Dev d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = (T*)smem_raw;
   FwdRec<T>* stage = (FwdRec<T>*)(smem_raw + (size_t)13 * RING * sizeof(T));
@@ -1008,7 +1064,7 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_sweep_fwd_quad(Dev d) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(NARROW_THREADS) k_sweep_bwd_quad(Dev d) {
+__global__ void __launch_bounds__(QUAD_THREADS) k_sweep_bwd_quad(Dev d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = (T*)smem_raw;
   BwdRec<T>* stage = (BwdRec<T>*)(smem_raw + (size_t)13 * RING * sizeof(T));

@@ -28,7 +28,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
                 ("check_every", C.c_int32), ("use_graph", C.c_int32), ("sweep_threads", C.c_int32),
                 ("timing", C.c_int32), ("sweep_mode", C.c_int32), ("sweep_cluster", C.c_int32),
-                ("groups", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("groups", C.c_int32), ("sweep_quad", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class Flow(C.Structure):
@@ -43,7 +43,8 @@ class Flow(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("sweep_threads", C.c_int32), ("flux_block", C.c_int32), ("sweep_mode", C.c_int32),
-                ("sweep_cluster", C.c_int32), ("ms_per_iter", C.c_float), ("groups", C.c_int32)]
+                ("sweep_cluster", C.c_int32), ("ms_per_iter", C.c_float), ("groups", C.c_int32),
+                ("sweep_quad", C.c_int32)]
 
 
 class Status(C.Structure):
@@ -219,10 +220,10 @@ class Context:
     """One igks_ctx: a set of steady solves resident on one GPU."""
 
     def __init__(self, precision=PREC_FP64, device=0, stream=None, check_every=20, use_graph=1,
-                 sweep_threads=0, timing=0, sweep_mode=0, sweep_cluster=0, groups=0):
+                 sweep_threads=0, timing=0, sweep_mode=0, sweep_cluster=0, groups=0, sweep_quad=0):
         o = Options(precision=precision, device=device, stream=stream, check_every=check_every,
                     use_graph=use_graph, sweep_threads=sweep_threads, timing=timing, sweep_mode=sweep_mode,
-                    sweep_cluster=sweep_cluster, groups=groups)
+                    sweep_cluster=sweep_cluster, groups=groups, sweep_quad=sweep_quad)
         h = C.c_void_p()
         rc = lib().igks_create(C.byref(o), C.byref(h))
         if rc:

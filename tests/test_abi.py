@@ -71,3 +71,16 @@ def test_footprint_bound_is_host_only_and_monotone():
     assert 0 < a < b
     # about 2 kB per cell for these meshes: one 250k-cell solve takes well under 1 GB
     assert 1500 < b / big.n_cells < 2500
+
+
+@pytest.mark.parametrize("bad", [dict(sweep_quad=2), dict(sweep_threads=512), dict(sweep_threads=1024, sweep_quad=1),
+                                 dict(sweep_threads=100), dict(precision=7), dict(sweep_cluster=3)])
+def test_create_rejects_bad_options_on_the_host(bad):
+    """igks_create checks its options before it touches a device (so this runs without a
+    GPU): a quad flag other than 0/1, more than 256 threads per sweep block without quads or
+    512 with them, a block that is not whole warps, an unknown precision or cluster size."""
+    from paper_1709_00803_gb300 import igks
+    o = igks.Options(**bad)
+    h = C.c_void_p()
+    assert igks.lib().igks_create(C.byref(o), C.byref(h)) == igks.EINVAL
+    assert not h.value
