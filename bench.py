@@ -257,11 +257,10 @@ def run_reference_batch(args, budget_s=150.0):
 
 
 def _given_launch(ctx, spec):
-    """Apply a launch configuration given as flux_block,sweep_threads,groups[,quad]."""
+    """Apply a launch configuration given as flux_block,sweep_threads,groups[,sweep_cluster]."""
     v = [int(x) for x in spec.split(",")]
-    fb, stt, gr, qd = (v + [0])[:4]
-    tuning = dict(sweep_threads=stt, flux_block=fb, sweep_mode=1, sweep_cluster=1, groups=gr, sweep_quad=qd,
-                  ms_per_iter=0.0)
+    fb, stt, gr, cl = (v + [1])[:4]
+    tuning = dict(sweep_threads=stt, flux_block=fb, sweep_mode=1, sweep_cluster=cl, groups=gr, ms_per_iter=0.0)
     ctx.set_launch(tuning)
     return tuning
 
@@ -512,7 +511,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other", action="store_true", help="skip the other precision / the flat plate")
     ap.add_argument("--no-serving", action="store_true", help="batch: skip the bounded serving leg")
-    ap.add_argument("--launch", default="", help="flux_block,sweep_threads,groups[,quad] instead of autotune")
+    ap.add_argument("--launch", default="", help="flux_block,sweep_threads,groups[,sweep_cluster] instead of autotune")
     ap.add_argument("--open-loop", type=int, default=1, help="serving: 1 Poisson arrivals after the capacity "
                     "run, 0 latencies of the capacity run")
     ap.add_argument("--plain-sample", type=int, default=0, help="serving: estimate the plain path from this many "
@@ -795,6 +794,11 @@ def main_serving(args):
         res_cap, T_cap = _serve(igks, cases, args)
     n_conv = sum(conv(r["state"]) for r in res_cap)
     cap_per_s = len(res_cap) / T_cap
+    # progress on stderr: the capacity run alone, in case a later phase is cut short
+    print(json.dumps({"phase": "capacity", "requests": len(res_cap), "converged": n_conv, "makespan_s": T_cap,
+                      "solves_per_hour": n_conv / T_cap * 3600.0,
+                      "iterations": [r["iters"] for r in res_cap], "states": [r["state"] for r in res_cap],
+                      "cells": [m.n_cells for m, _, _ in cases]}), file=sys.stderr, flush=True)
     # open loop: Poisson arrivals at 0.8 x the measured capacity
     gaps = np.array([sp["gap"] for _, _, sp in cases])
     arrivals = np.cumsum(gaps) / (0.8 * cap_per_s) if args.open_loop else np.zeros(len(cases))

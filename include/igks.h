@@ -84,11 +84,13 @@ typedef struct igks_options {
                              consecutive solves (0: 1), each iterated by a graph on a stream of
                              its own, so that one group's sweeps (one block per solve) overlap
                              another group's flux; same arithmetic, same bits */
-  int32_t sweep_quad;     /* schedule 1 with sweep_cluster 1, FP32 and double-float sweeps: a quad
-                             of threads per cell (component k on thread k of the quad), so that a
-                             block of sweep_threads (<= 512) threads holds sweep_threads / 4 cells
-                             of a level; same arithmetic, same bits; ignored for FP64 sweeps */
-  int32_t reserved[2];
+  int32_t wait_limit;     /* tries of a device wait (the one-block-per-solve sweeps wait on an
+                             mbarrier for each level's records) before it gives up: the solve
+                             stops with state IGKS_TIMEOUT, its fields untouched, and
+                             igks_iterate returns IGKS_TIMEOUT (0: about a second) */
+  int32_t starve_test;    /* test hook, 0 in use: 1 makes every forward sweep skip the copy of
+                             its second level, so that the wait for it runs out */
+  int32_t reserved[1];
 } igks_options;
 
 /* Flow conditions of one solve. Non-dimensional: free-stream density, speed and the
@@ -154,7 +156,9 @@ int igks_init_freestream(igks_ctx* ctx, int32_t solve);
  * (res_l2_rel <= res_target, or the Eq. 40 ratio <= eq40_target when that is set) or
  * divergence; the host checks every check_every iterations. status (nullable) receives
  * one entry per solve. Returns IGKS_CONVERGED if every solve has converged, IGKS_OK if
- * some are still running, IGKS_DIVERGED if any diverged, or another error. */
+ * some are still running, IGKS_TIMEOUT if a solve's sweep wait ran out of its spin limit
+ * (that solve stops with its fields as they were before the iteration; the context stays
+ * usable), IGKS_DIVERGED if any diverged, or another error. */
 int igks_iterate(igks_ctx* ctx, int32_t max_iters, igks_status* status);
 
 /* Enqueue n_iters iterations of every live solve on the context stream and return at
@@ -233,7 +237,6 @@ typedef struct igks_tuning {
   int32_t sweep_cluster;   /* blocks per solve of schedule 1 */
   float ms_per_iter;       /* measured device time of one iteration with it */
   int32_t groups;          /* groups of solves on streams of their own (igks_options.groups) */
-  int32_t sweep_quad;      /* a quad of threads per cell (igks_options.sweep_quad) */
 } igks_tuning;
 
 /* Time the library's launch configurations (sweep schedule, block size and blocks per

@@ -465,33 +465,41 @@ static int build(igks_ctx* ctx) {
   }
   // ---- narrow schedule: per-position padded stencils (PF_E entries) and positions ----
   const int P = (int)fwd_order.size();
-  std::vector<int> pos_f(nc, -1), pos_b(nc, -1), pb_of_pf(P), cnt_f(P), cnt_b(P);
-  std::vector<int> ej_f((size_t)PF_E * P, 0), eslot_f((size_t)PF_E * P, -1);
-  std::vector<int> ej_b((size_t)PF_E * P, 0), eslot_b((size_t)PF_E * P, -1);
+  std::vector<int> pos_f(nc, -1), pos_b(nc, -1);
+  std::vector<FwdStat> fst(P);
+  std::vector<BwdStat> bst(P);
   std::vector<int> cf_to_ef(cf_face.size(), -1), cf_to_eb(cf_face.size(), -1);
   for (int p = 0; p < P; p++) { pos_f[fwd_order[p]] = p; pos_b[bwd_order[p]] = p; }
-  for (int p = 0; p < P; p++) pb_of_pf[p] = pos_b[fwd_order[p]];
+  for (int p = 0; p < P; p++) {
+    FwdStat& f = fst[p];
+    BwdStat& b = bst[p];
+    std::memset(&f, 0, sizeof f);
+    std::memset(&b, 0, sizeof b);
+    f.i = fwd_order[p]; f.pb = pos_b[fwd_order[p]];
+    b.i = bwd_order[p];
+    for (int e = 0; e < PF_E; e++) { f.slot[e] = -1; b.slot[e] = -1; }
+  }
   for (int dir = 0; dir < 2; dir++) {
     const bool fwd = dir == 0;
     const std::vector<int>& sptr = fwd ? fs_ptr : bs_ptr;
     const std::vector<int>& sj = fwd ? fs_j : bs_j;
     const std::vector<int>& sslot = fwd ? fs_slot : bs_slot;
     const std::vector<int>& map = fwd ? cf_to_fs : cf_to_bs;
-    std::vector<int>& cnt = fwd ? cnt_f : cnt_b;
-    std::vector<int>& ej = fwd ? ej_f : ej_b;
-    std::vector<int>& es = fwd ? eslot_f : eslot_b;
     std::vector<int>& emap = fwd ? cf_to_ef : cf_to_eb;
     std::vector<int> inv(sj.size(), -1);
     for (size_t k = 0; k < map.size(); k++)
       if (map[k] >= 0) inv[map[k]] = (int)k;
     for (int p = 0; p < P; p++) {
+      int* cnt = fwd ? &fst[p].cnt : &bst[p].cnt;
+      int* ej = fwd ? fst[p].j : bst[p].j;
+      int* es = fwd ? fst[p].slot : bst[p].slot;
       const int q0 = sptr[p], m_ = sptr[p + 1] - q0;
-      if (m_ > PF_E) { cnt[p] = -1; continue; }
-      cnt[p] = m_;
+      if (m_ > PF_E) { *cnt = -1; continue; }
+      *cnt = m_;
       for (int e = 0; e < m_; e++) {
-        ej[(size_t)e * P + p] = sj[q0 + e];
-        es[(size_t)e * P + p] = sslot[q0 + e];
-        emap[inv[q0 + e]] = e * P + p;
+        ej[e] = sj[q0 + e];
+        es[e] = sslot[q0 + e];
+        emap[inv[q0 + e]] = p * PF_E + e;
       }
     }
   }
@@ -523,7 +531,9 @@ static int build(igks_ctx* ctx) {
   AL(st, SolveState, ns); AL(dt_bits, unsigned long long, ns);
   AL(part, double, 2 * (size_t)d.n_cell_blocks); AL(err, int, 4);
   AL(hist, double, 2 * (size_t)HIST * ns);
-  AL(eq40_bits, unsigned long long, ns); AL(bad, int, ns);
+  AL(eq40_bits, unsigned long long, ns); AL(bad, int, ns); AL(tmo, int, ns);
+  d.wait_limit = ctx->opt.wait_limit > 0 ? ctx->opt.wait_limit : DEFAULT_WAIT_LIMIT;
+  d.starve_test = ctx->opt.starve_test;
   d.nnz = (int)cf_face.size();
   AL(sw_cell, double, 5 * (size_t)nc); AL(sw_st, double, 4 * (size_t)d.nnz); AL(sw_j, int, d.nnz);
   UP(fs_ptr, fs_ptr); UP(fs_j, fs_j); UP(fs_slot, fs_slot); UP(cf_to_fs, cf_to_fs);
@@ -532,12 +542,11 @@ static int build(igks_ctx* ctx) {
   d.nbs = (int)bs_j.size();
   AL(sc_f, double, 4 * (size_t)std::max(d.nfs, 1)); AL(sc_b, double, 4 * (size_t)std::max(d.nbs, 1));
   d.npos = P;
-  UP(pos_f, pos_f); UP(pos_b, pos_b); UP(pb_of_pf, pb_of_pf); UP(cnt_f, cnt_f); UP(cnt_b, cnt_b);
-  UP(ej_f, ej_f); UP(eslot_f, eslot_f); UP(ej_b, ej_b); UP(eslot_b, eslot_b);
+  UP(pos_f, pos_f); UP(pos_b, pos_b); UP(fst, fst); UP(bst, bst);
   UP(cf_to_ef, cf_to_ef); UP(cf_to_eb, cf_to_eb);
-  AL(rec_f, double, 13 * (size_t)P); AL(rec_b, double, 15 * (size_t)P);
+  // per-iteration records, sized for the widest sweep type
+  AL(fdyn, FwdDyn<double>, (size_t)P); AL(bdyn, BwdDyn<double>, (size_t)P);
   AL(gprim, double, 6 * (size_t)nf);
-  AL(ec_f, double, 4 * (size_t)PF_E * P); AL(ec_b, double, 4 * (size_t)PF_E * P);
   setup_sweeps();
   {
     // wide schedule: level l of every solve, solves in order
@@ -549,7 +558,6 @@ static int build(igks_ctx* ctx) {
     int mode = ctx->opt.sweep_mode;
     d.wide = (mode == 2) || (mode == 0 && std::max(maxf, maxb) <= WIDE_MAX_LEVELS);
     d.sweep_cluster = ctx->opt.sweep_cluster;
-    d.quad = ctx->opt.sweep_quad != 0 && ctx->opt.precision != IGKS_PREC_FP64;
     std::vector<int> wf, wb;
     ctx->h_wfwd_ptr.assign(1, 0);
     ctx->h_wbwd_ptr.assign(1, 0);
@@ -624,8 +632,8 @@ int igks_create(const igks_options* opt, igks_ctx** out) {
   if (opt) ctx->opt = *opt;
   if (ctx->opt.check_every <= 0) ctx->opt.check_every = 20;
   if (ctx->opt.sweep_threads <= 0) ctx->opt.sweep_threads = NARROW_THREADS;
-  if (ctx->opt.sweep_quad != 0 && ctx->opt.sweep_quad != 1) { delete ctx; return IGKS_EINVAL; }
-  if (ctx->opt.sweep_threads > (ctx->opt.sweep_quad ? QUAD_THREADS : NARROW_THREADS) || ctx->opt.sweep_threads % 32) {
+  if (ctx->opt.sweep_threads > NARROW_THREADS || ctx->opt.sweep_threads % 32) { delete ctx; return IGKS_EINVAL; }
+  if (ctx->opt.wait_limit < 0 || (ctx->opt.starve_test != 0 && ctx->opt.starve_test != 1)) {
     delete ctx;
     return IGKS_EINVAL;
   }
@@ -827,6 +835,8 @@ int igks_iterate(igks_ctx* ctx, int32_t max_iters, igks_status* status) {
     all_conv &= (q.state == IGKS_CONVERGED);
     any_div |= (q.state < 0);
   }
+  for (int s = 0; s < ns; s++)
+    if (ctx->h_st[s].state == IGKS_TIMEOUT) return fail(ctx, IGKS_TIMEOUT, "a sweep wait ran out of its spin limit");
   if (any_div) return IGKS_DIVERGED;
   return all_conv ? IGKS_CONVERGED : IGKS_OK;
 }
@@ -1094,28 +1104,21 @@ int igks_autotune(igks_ctx* ctx, int32_t iters_per_trial, igks_tuning* out) {
   best.ms_per_iter = 1e30f;
   const bool wide_ok = std::max(d.n_wfwd, d.n_wbwd) <= 4 * WIDE_MAX_LEVELS;
   const int flux_blocks[] = {64, 128};
-  // narrow-schedule blocks: one thread per cell (128, 256 threads) and, for FP32 and
-  // double-float sweeps, a quad of threads per cell (256, 512 threads)
-  const int blocks[][2] = {{128, 0}, {256, 0}, {256, 1}, {512, 1}};
-  const bool quad_ok = ctx->opt.precision != IGKS_PREC_FP64;
+  const int sweep_threads[] = {128, 256};
   const int clusters[] = {1, 2, 4};
   const int groups[] = {1, 2, 4};
   int err = 0;
   for (int wide = 0; wide <= (wide_ok ? 1 : 0) && !err; wide++)
     for (int fb : flux_blocks)
-      for (const auto& blk : blocks)
+      for (int stt : sweep_threads)
         for (int cl : clusters)
           for (int gr : groups) {
-          const int stt = blk[0], qd = blk[1];
-          if (wide && (blk != blocks[0] || cl != 1 || gr != 1)) continue;   // the wide schedule has its own block
+          if (wide && (stt != sweep_threads[0] || cl != 1 || gr != 1)) continue;   // the wide schedule has its own block
           if (gr > 1 && (cl != 1 || gr > ns)) continue;
-          if (qd && (!quad_ok || cl != 1)) continue;
           d.wide = wide;
           d.flux_block = fb;
           d.sweep_cluster = cl;
-          d.quad = qd;
           ctx->opt.sweep_threads = stt;
-          ctx->opt.sweep_quad = qd;
           ctx->opt.groups = gr;
           if ((err = recapture(ctx))) break;
           restore();
@@ -1127,17 +1130,15 @@ int igks_autotune(igks_ctx* ctx, int32_t iters_per_trial, igks_tuning* out) {
           float ms = 0.0f;
           cudaEventElapsedTime(&ms, e0, e1);
           ms /= iters_per_trial;
-          if (ms < best.ms_per_iter) best = igks_tuning{stt, fb, wide ? 2 : 1, cl, ms, gr, qd};
+          if (ms < best.ms_per_iter) best = igks_tuning{stt, fb, wide ? 2 : 1, cl, ms, gr};
           }
   // apply the winner and put every solve back where it was
   d.wide = best.sweep_mode == 2;
   d.flux_block = best.flux_block;
   d.sweep_cluster = best.sweep_cluster;
-  d.quad = best.sweep_quad;
   ctx->opt.sweep_threads = best.sweep_threads;
   ctx->opt.sweep_mode = best.sweep_mode;
   ctx->opt.sweep_cluster = best.sweep_cluster;
-  ctx->opt.sweep_quad = best.sweep_quad;
   ctx->opt.groups = best.groups;
   if (!err) err = recapture(ctx);
   restore();
@@ -1155,11 +1156,7 @@ int igks_autotune(igks_ctx* ctx, int32_t iters_per_trial, igks_tuning* out) {
 
 int igks_set_launch(igks_ctx* ctx, const igks_tuning* t) {
   if (!ctx || !t) return IGKS_EINVAL;
-  const bool quad = t->sweep_quad == 1;
-  if ((t->sweep_quad != 0 && !quad) ||
-      (quad ? (t->sweep_threads != 256 && t->sweep_threads != 512)
-            : (t->sweep_threads != 128 && t->sweep_threads != 256)) ||
-      (t->flux_block != 64 && t->flux_block != 128) ||
+  if ((t->sweep_threads != 128 && t->sweep_threads != 256) || (t->flux_block != 64 && t->flux_block != 128) ||
       (t->sweep_mode != 1 && t->sweep_mode != 2) ||
       (t->sweep_cluster != 1 && t->sweep_cluster != 2 && t->sweep_cluster != 4 && t->sweep_cluster != 8) ||
       t->groups < 1)
@@ -1170,11 +1167,9 @@ int igks_set_launch(igks_ctx* ctx, const igks_tuning* t) {
   d.wide = t->sweep_mode == 2;
   d.flux_block = t->flux_block;
   d.sweep_cluster = t->sweep_cluster;
-  d.quad = quad && ctx->opt.precision != IGKS_PREC_FP64;
   ctx->opt.sweep_threads = t->sweep_threads;
   ctx->opt.sweep_mode = t->sweep_mode;
   ctx->opt.sweep_cluster = t->sweep_cluster;
-  ctx->opt.sweep_quad = t->sweep_quad;
   ctx->opt.groups = t->groups;
   return recapture(ctx);
 }
@@ -1200,11 +1195,12 @@ int igks_footprint_bytes(int32_t n_nodes, int32_t n_cells, int32_t n_faces, int3
   if (n_nodes <= 0 || n_cells <= 0 || n_faces <= 0 || nnz < 0 || !out) return IGKS_EINVAL;
   const int64_t ncp = (int64_t)(n_cells + CELL_ALIGN - 1) / CELL_ALIGN * CELL_ALIGN;
   // (plus 16 KiB of residual history per solve, in the fixed part below)
-  // per padded cell: 122 doubles (state, gradients, speeds, increments, sweep records) +
-  // 32 ints (CSR pointers, orders, levels, positions, padded stencils); per CSR entry 60 B
-  // (face and node lists, sweep stencil coefficients, maps) + 40 B (one sweep entry); per
-  // face 34 doubles + 8 ints; per node 2 doubles; a few hundred bytes per solve
-  *out = 1104 * ncp + 100 * (int64_t)nnz + 304 * (int64_t)n_faces + 16 * (int64_t)n_nodes + 4096 + 16384;
+  // per padded cell: 62 doubles (state, gradients, speeds, increments, cell constants),
+  // the sweep records (2 x 48 B static, 240 + 272 B per iteration), 9 ints (CSR pointers,
+  // orders, levels, positions) and 16 B to spare; per CSR entry 60 B (face and node lists, sweep
+  // stencil coefficients, maps) + 40 B (one sweep entry); per face 34 doubles + 8 ints; per
+  // node 2 doubles; a few hundred bytes per solve
+  *out = 1156 * ncp + 100 * (int64_t)nnz + 304 * (int64_t)n_faces + 16 * (int64_t)n_nodes + 4096 + 16384;
   return IGKS_OK;
 }
 

@@ -485,6 +485,8 @@ __global__ void k_end_iter(Dev d) {
   const double e40 = d.flow[s].eq40_target;
   if (st.pending == 0 && e40 > 0.0 && st.eq40 <= e40) st.pending = 1;   // Eq. 40 criterion
   if (d.bad[s]) st.pending = -5;   // IGKS_DIVERGED
+  if (d.tmo[s]) st.pending = -6;   // IGKS_TIMEOUT: a sweep wait ran out, the state was kept
+  d.tmo[s] = 0;
   st.iter += 1;
   st.state = st.pending;
   d.dt_bits[s] = 0x7FF0000000000000ull;   // +inf: the next iteration's minimum starts here

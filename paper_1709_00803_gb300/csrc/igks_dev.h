@@ -31,6 +31,26 @@ struct DevFlow {
 };
 
 // per-solve iteration state, updated only on the device during iterations
+constexpr int PF_E = 4;              // stencil entries held per sweep record
+
+// static part of a narrow-sweep record: cell, entry count (-1: CSR stencil), the cell's
+// backward position, and the entries' neighbours (j < 0: wall / symmetry ghost of face
+// -1 - j) and shared-memory ring slots (-1: read from global memory)
+struct alignas(16) FwdStat { int i, cnt, pb, pad; int j[PF_E], slot[PF_E]; };
+struct alignas(16) BwdStat { int i, cnt, pad0, pad1; int j[PF_E], slot[PF_E]; };
+// per-iteration part (T = double, float or double-float): forward: residual M[5], state
+// (r, mx, my), 1/D, 1/a_ii, u, v, H and per entry (sx, sy, s lambda, SA coefficient);
+// backward: state W[5], the same five constants, the forward increment dW*[5], entries.
+// Every record is an odd number of 16-byte chunks, so a warp reading its lanes' records
+// from shared memory with 16-byte loads hits distinct banks.
+template <class T>
+struct alignas(16) FwdDyn { T m[5], w[3], c[5]; T co[4][PF_E]; T pad[sizeof(T) == 4 ? 7 : 1]; };
+template <class T>
+struct alignas(16) BwdDyn { T w[5], c[5], ws[5]; T co[4][PF_E]; T pad[sizeof(T) == 4 ? 5 : 3]; };
+static_assert(sizeof(FwdStat) == 48 && sizeof(BwdStat) == 48, "static record size");
+static_assert(sizeof(FwdDyn<float>) == 144 && sizeof(FwdDyn<double>) == 240, "forward record size");
+static_assert(sizeof(BwdDyn<float>) == 144 && sizeof(BwdDyn<double>) == 272, "backward record size");
+
 struct SolveState {
   double dt, cfl, res_inf, res_l2, res_l2_first, res_inf_prev, eq40;
   int iter;
@@ -101,22 +121,23 @@ struct Dev {
   const int* bs_ptr; const int* bs_j; const int* bs_slot; const int* cf_to_bs;
   void* sc_f; void* sc_b;        // [4][entries] coefficients (T), written by the pre-pass
   int nfs, nbs;                  // entry counts
-  // narrow schedule, per sweep position p (P = npos = all real cells): records of
-  // per-iteration data in position-major SoA, and up to PF_E stencil entries padded per
-  // position (cnt < 0: more entries than that, use the CSR stencil above)
+  // narrow schedule, per sweep position p (P = npos = all real cells): one record per
+  // position and direction, array-of-structures so that a level's records are one
+  // contiguous range (one bulk copy); the static part (cell, entry count, neighbours,
+  // ring slots) is uploaded once, the per-iteration part written by the pre-pass. Up to
+  // PF_E stencil entries per record (cnt < 0: more than that, use the CSR stencil above).
   int npos;
   const int* pos_f; const int* pos_b;            // [nc_pad] position of a cell (-1 padding)
-  void* rec_f;                                   // [13][P] T: M[5], r, mx, my, 1/D, 1/a_ii, u, v, H
+  const FwdStat* fst; const BwdStat* bst;        // [P]
+  void* fdyn; void* bdyn;                        // [P] FwdDyn<T> / BwdDyn<T>
   void* gprim;                                   // [6][nf] T: ghost r, mx, my, u, v, H of wall/symmetry faces
-  void* rec_b;                                   // [15][P] T: W[5], 1/D, 1/a_ii, u, v, H, dW*[5]
-  void* ec_f; void* ec_b;                        // [4][PF_E][P] T: sx, sy, s lambda, SA coefficient
-  const int* cnt_f; const int* ej_f; const int* eslot_f; const int* pb_of_pf;
-  const int* cnt_b; const int* ej_b; const int* eslot_b;
-  const int* cf_to_ef; const int* cf_to_eb;      // [nnz] e * P + p, or -1
+  const int* cf_to_ef; const int* cf_to_eb;      // [nnz] p * PF_E + e, or -1
+  int wait_limit;                // spins of a device wait before it gives up (IGKS_TIMEOUT)
+  int starve_test;               // test hook: the forward sweep never stages its second level
+  int* tmo;                      // [n_solves] a sweep wait of the solve ran out this iteration
   // wide schedule: cells of each level of all solves
   int wide;                      // 1: one launch per level; 0: one block per solve
   int sweep_cluster;             // narrow schedule: blocks (a thread-block cluster) per solve
-  int quad;                      // narrow FP32 / double-float sweeps: a quad of threads per cell
   const int* wfwd_cells; const int* wbwd_cells;
   const int* h_wfwd_ptr; const int* h_wbwd_ptr;   // HOST arrays of level offsets (launch sizes)
   int n_wfwd, n_wbwd;
@@ -157,9 +178,8 @@ void launch_update(const Dev& d, int precision, cudaStream_t s);
 void launch_end_iter(const Dev& d, cudaStream_t s);
 constexpr int N_KERNEL_KINDS = 11;   // kernels of one iteration (the wide sweeps launch per level)
 constexpr int RING = 1024;           // shared-memory ring of the narrow sweeps (cells)
-constexpr int PF_E = 4;              // stencil entries held per prefetched sweep position
 constexpr int NARROW_THREADS = 256;  // block of the narrow sweeps (one thread per cell of a level)
-constexpr int QUAD_THREADS = 512;    // block of the narrow sweeps with a quad of threads per cell
+constexpr int DEFAULT_WAIT_LIMIT = 1 << 24;   // spins of a device wait (about a second)
 constexpr int WIDE_MAX_LEVELS = 64;  // automatic choice: wide schedule up to this many levels
 constexpr int HIST = 1024;           // iterations of residual history kept per solve
 

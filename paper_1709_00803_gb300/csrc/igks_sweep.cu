@@ -34,7 +34,7 @@ namespace igks {
 // The sweeps' arithmetic is written with explicitly rounded operations (fma_x, mul_x,
 // add_x: __fma_rn / __dmul_rn / __dadd_rn in FP64, the __f*_rn intrinsics in FP32, the
 // double-float operators): the compiler may not fuse or split them, so every schedule (one
-// thread per cell, a quad of threads per cell, one launch per level) and every inlining
+// block or a cluster of blocks per solve, one launch per level) and every inlining
 // context gives the same bits for the same cell.
 __device__ __forceinline__ double fma_x(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ double mul_x(double a, double b) { return __dmul_rn(a, b); }
@@ -196,18 +196,18 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_sweep_prep(Dev d) {
     for (int q = 0; q < 5; q++) c[q * n + i] = cc[q];
   }
   // position-ordered records of the narrow schedule
-  const int P = d.npos, pf = d.pos_f[i], pb = d.pos_b[i];
-  const bool csr_f = d.cnt_f[pf] < 0, csr_b = d.cnt_b[pb] < 0;   // more entries than a record holds
+  const int pf = d.pos_f[i], pb = d.pos_b[i];
+  FwdDyn<T>* rf = (FwdDyn<T>*)d.fdyn + pf;
+  BwdDyn<T>* rb = (BwdDyn<T>*)d.bdyn + pb;
+  const bool csr_f = d.fst[pf].cnt < 0, csr_b = d.bst[pb].cnt < 0;   // more entries than a record holds
   if (!wide) {
-    T* rf = (T*)d.rec_f;
-    T* rb = (T*)d.rec_b;
 #pragma unroll
-    for (int q = 0; q < 5; q++) rf[q * P + pf] = (T)d.M[q * n + i];
-    rf[5 * P + pf] = (T)r; rf[6 * P + pf] = (T)mx; rf[7 * P + pf] = (T)my;
+    for (int q = 0; q < 5; q++) rf->m[q] = (T)d.M[q * n + i];
+    rf->w[0] = (T)r; rf->w[1] = (T)mx; rf->w[2] = (T)my;
 #pragma unroll
-    for (int q = 0; q < 5; q++) { rf[(8 + q) * P + pf] = cc[q]; rb[(5 + q) * P + pb] = cc[q]; }
+    for (int q = 0; q < 5; q++) { rf->c[q] = cc[q]; rb->c[q] = cc[q]; }
 #pragma unroll
-    for (int q = 0; q < 5; q++) rb[q * P + pb] = (T)d.W[q * n + i];
+    for (int q = 0; q < 5; q++) rb->w[q] = (T)d.W[q * n + i];
   }
   T* sc = (T*)d.sw_st;
   const int nnz = d.nnz;
@@ -234,15 +234,16 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_sweep_prep(Dev d) {
         T* o = (T*)d.sc_b;
         o[eb] = e0; o[d.nbs + eb] = e1; o[2 * d.nbs + eb] = e2; o[3 * d.nbs + eb] = e3;
       }
-      const size_t PE = (size_t)PF_E * d.npos;
-      const int xf = d.cf_to_ef[k], xb = d.cf_to_eb[k];
+      const int xf = d.cf_to_ef[k], xb = d.cf_to_eb[k];   // record entry: position * PF_E + e
       if (xf >= 0) {
-        T* o = (T*)d.ec_f;
-        o[xf] = e0; o[PE + xf] = e1; o[2 * PE + xf] = e2; o[3 * PE + xf] = e3;
+        T (*co)[PF_E] = ((FwdDyn<T>*)d.fdyn)[xf / PF_E].co;
+        const int e = xf % PF_E;
+        co[0][e] = e0; co[1][e] = e1; co[2][e] = e2; co[3][e] = e3;
       }
       if (xb >= 0) {
-        T* o = (T*)d.ec_b;
-        o[xb] = e0; o[PE + xb] = e1; o[2 * PE + xb] = e2; o[3 * PE + xb] = e3;
+        T (*co)[PF_E] = ((BwdDyn<T>*)d.bdyn)[xb / PF_E].co;
+        const int e = xb % PF_E;
+        co[0][e] = e0; co[1][e] = e1; co[2][e] = e2; co[3][e] = e3;
       }
     }
     // the ghost state of a wall or symmetry face in the form the backward sweep's flux
@@ -345,7 +346,9 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_update(Dev d) {
   const int s = d.cell_solve[blk * CELL_BLOCK];   // every block lies in one solve
   double eq40 = 0.0;
   int bad = 0;
-  const bool live = (i < d.nc_pad) && d.cell_solve[i] >= 0 && d.st[d.cell_solve[i]].state == 0;
+  // a solve whose sweep wait ran out keeps its state (the increments are incomplete)
+  const bool live = (i < d.nc_pad) && d.cell_solve[i] >= 0 && d.st[d.cell_solve[i]].state == 0 &&
+                    !d.tmo[d.cell_solve[i]];
   if (live) {
     const int n = d.nc_pad;
     const T* dWo = (const T*)d.dW;
@@ -401,10 +404,14 @@ __device__ __forceinline__ void flush_eq40(const Dev& d, int s, double eq40, int
 // ring layout: [13][RING] of T: the 8 flux increments, then the 5 variable increments of
 // the cell at sweep position p (local to the solve), stored at slot p % RING.
 //
-// Per-position records (written by the pre-pass, position-major SoA so one level's
-// records are contiguous) are prefetched into registers one level ahead: the block
-// issues the loads of level l+1 before it works on level l, so by the time level l+1
-// starts only the neighbours' increments (shared-memory ring) sit on the dependency chain.
+// Records. Each position has a static record (cell, neighbours, ring slots; 48 bytes) and
+// a per-iteration record (FwdDyn / BwdDyn: 128 bytes in FP32, 240 / 256 in FP64 and
+// double-float), both arrays of structures, so the records of one level are two contiguous
+// ranges. With one block per solve the block brings a level's records into shared memory
+// with two bulk copies (cp.async.bulk, the TMA engine's linear copy) completing on an
+// mbarrier, NST levels ahead; the cells' threads only wait on the barrier and read. With a
+// cluster of blocks per solve each thread stages its own record with 16-byte cp.async one
+// level ahead.
 template <class T>
 __device__ __forceinline__ void ring_put(T* ring, int slot, const T* o, const T* dw) {
 #pragma unroll
@@ -445,95 +452,79 @@ __device__ __forceinline__ void neighbour(const Dev& d, const T* ring, const T* 
   }
 }
 
-// Each cell of a level is handled by one thread. Its record (per-iteration data and up
-// to PF_E stencil entries) is staged into shared memory by cp.async one level ahead.
+static_assert(sizeof(FwdDyn<df64>) == sizeof(FwdDyn<double>) && sizeof(BwdDyn<df64>) == sizeof(BwdDyn<double>),
+              "double-float records");
 
-// asynchronous global -> shared copies (cp.async, 4 or 8 bytes): the copy proceeds in the
-// background and never holds registers, so the next level's records are in flight while
-// the current level is computed
-template <class U>
-__device__ __forceinline__ void cpa(U* dst_smem, const U* src) {
-  static_assert(sizeof(U) == 4 || sizeof(U) == 8, "cp.async element size");
+// ---- asynchronous copies ----
+// 16-byte cp.async (cluster schedule): global -> shared in the background, no registers held
+__device__ __forceinline__ void cpa16(void* dst_smem, const void* src) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(dst_smem);
-  if (sizeof(U) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
-  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// forward record of one position: residual, state (r, mx, my), 1/D, 1/a_ii, u, v, H, cell,
-// entry count, backward position, and PF_E stencil entries
-template <class T>
-struct FwdRec {
-  T m[5], w[3], c[5];
-  T co[4][PF_E];
-  int i, cnt, pb, pad;
-  int j[PF_E], slot[PF_E];
-};
-
-template <class T>
-__device__ __forceinline__ void fwd_stage(const Dev& d, int p, FwdRec<T>* st) {
-  const int P = d.npos;
-  const T* rec = (const T*)d.rec_f;
-  const T* ec = (const T*)d.ec_f;
+// a record into registers with 16-byte loads (shared or global memory)
+template <class R>
+__device__ __forceinline__ R load_rec(const R* src) {
+  R r;
 #pragma unroll
-  for (int v = 0; v < 5; v++) cpa(&st->m[v], rec + v * P + p);
-#pragma unroll
-  for (int v = 0; v < 3; v++) cpa(&st->w[v], rec + (5 + v) * P + p);
-#pragma unroll
-  for (int v = 0; v < 5; v++) cpa(&st->c[v], rec + (8 + v) * P + p);
-  cpa(&st->i, d.fwd_order + p);
-  cpa(&st->cnt, d.cnt_f + p);
-  cpa(&st->pb, d.pb_of_pf + p);
-#pragma unroll
-  for (int e = 0; e < PF_E; e++) {
-    cpa(&st->j[e], d.ej_f + e * P + p);
-    cpa(&st->slot[e], d.eslot_f + e * P + p);
-#pragma unroll
-    for (int k = 0; k < 4; k++) cpa(&st->co[k][e], ec + (k * PF_E + e) * P + p);
-  }
-  cpa_commit();
+  for (int k = 0; k < (int)(sizeof(R) / 16); k++) reinterpret_cast<uint4*>(&r)[k] = reinterpret_cast<const uint4*>(src)[k];
+  return r;
 }
 
-template <class T>
-__device__ __forceinline__ void fwd_load_direct(const Dev& d, int p, FwdRec<T>* st) {
-  const int P = d.npos;
-  const T* rec = (const T*)d.rec_f;
-  const T* ec = (const T*)d.ec_f;
+template <class R>
+__device__ __forceinline__ void cpa_record(R* dst, const R* src) {   // sizeof(R) is a multiple of 16
 #pragma unroll
-  for (int v = 0; v < 5; v++) st->m[v] = rec[v * P + p];
-#pragma unroll
-  for (int v = 0; v < 3; v++) st->w[v] = rec[(5 + v) * P + p];
-#pragma unroll
-  for (int v = 0; v < 5; v++) st->c[v] = rec[(8 + v) * P + p];
-  st->i = d.fwd_order[p];
-  st->cnt = d.cnt_f[p];
-  st->pb = d.pb_of_pf[p];
-#pragma unroll
-  for (int e = 0; e < PF_E; e++) {
-    st->j[e] = d.ej_f[e * P + p];
-    st->slot[e] = d.eslot_f[e * P + p];
-#pragma unroll
-    for (int k = 0; k < 4; k++) st->co[k][e] = ec[(k * PF_E + e) * P + p];
-  }
+  for (int k = 0; k < (int)(sizeof(R) / 16); k++) cpa16((char*)dst + 16 * k, (const char*)src + 16 * k);
 }
 
+// mbarrier and bulk copy (one block per solve)
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned bar, unsigned bytes) {   // the producer's arrival
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// wait for a phase of the barrier, at most limit tries; false when it ran out
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, int limit) {
+  for (int it = 0; it < limit; it++)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// ---- the work on one position (forward / backward), records in shared or global memory ----
 template <class T, int C = 1>
-__device__ __forceinline__ void fwd_process(const Dev& d, T* ring, int p, int pbase, const FwdRec<T>* r, bool sa_on) {
-  const int n = d.nc_pad, P = d.npos;
+__device__ __forceinline__ void fwd_process(const Dev& d, T* ring, int p, int pbase, const FwdStat& st,
+                                            const FwdDyn<T>& dy, bool sa_on) {
+  const int n = d.nc_pad;
   T* dWs = (T*)d.dWs;
   T* dF = (T*)d.dF;
   T acc[5];
 #pragma unroll
-  for (int v = 0; v < 5; v++) acc[v] = r->m[v];
-  const int cnt = r->cnt;
+  for (int v = 0; v < 5; v++) acc[v] = dy.m[v];
+  const int cnt = st.cnt;
   if (cnt >= 0) {
 #pragma unroll
     for (int e = 0; e < PF_E; e++) {
       if (e >= cnt) break;
       T f[8], w[5];
-      neighbour<T, C>(d, ring, dF, dWs, r->j[e], r->slot[e], f, w);
-      fwd_acc<T>(acc, r->co[0][e], r->co[1][e], r->co[2][e], r->co[3][e], f, w, sa_on);
+      neighbour<T, C>(d, ring, dF, dWs, st.j[e], st.slot[e], f, w);
+      fwd_acc<T>(acc, dy.co[0][e], dy.co[1][e], dy.co[2][e], dy.co[3][e], f, w, sa_on);
     }
   } else {
     // more entries than the record holds: the position-ordered CSR stencil
@@ -547,141 +538,28 @@ __device__ __forceinline__ void fwd_process(const Dev& d, T* ring, int p, int pb
   }
   T dw[5];
 #pragma unroll
-  for (int v = 0; v < 4; v++) dw[v] = inc_fwd<T>(acc[v], r->c[0]);
-  dw[4] = sa_on ? inc_fwd<T>(acc[4], r->c[1]) : (T)0;
+  for (int v = 0; v < 4; v++) dw[v] = inc_fwd<T>(acc[v], dy.c[0]);
+  dw[4] = sa_on ? inc_fwd<T>(acc[4], dy.c[1]) : (T)0;
   T o[8];
-  delta_flux<T>(r->w[0], r->w[1], r->w[2], r->c[2], r->c[3], r->c[4], dw[0], dw[1], dw[2], dw[3], o);
+  delta_flux<T>(dy.w[0], dy.w[1], dy.w[2], dy.c[2], dy.c[3], dy.c[4], dw[0], dw[1], dw[2], dw[3], o);
   const int slot = (p - pbase) % RING;
   ring_put<T>(ring, slot, o, dw);
-  const int i = r->i, pb = r->pb;
-  T* recb = (T*)d.rec_b;
+  const int i = st.i;
+  BwdDyn<T>* rb = (BwdDyn<T>*)d.bdyn + st.pb;
 #pragma unroll
   for (int v = 0; v < 5; v++) {
     dWs[v * n + i] = dw[v];
-    recb[(10 + v) * P + pb] = dw[v];          // the backward sweep's copy of dW*
+    rb->ws[v] = dw[v];                        // the backward sweep's copy of dW*
   }
 #pragma unroll
   for (int k = 0; k < 8; k++) dF[k * n + i] = o[k];
 }
 
-// the first position at or after b that belongs to cluster block r (positions q = p - pbase
-// are dealt round the C blocks: q % C == r)
-template <int C>
-__device__ __forceinline__ int first_own(int b, int pbase, int r) {
-  if constexpr (C == 1) return b;
-  return b + (((r - (b - pbase)) % C) + C) % C;
-}
-
-template <int C>
-__device__ __forceinline__ void level_barrier() {
-  if constexpr (C == 1) __syncthreads();
-  else cg::this_cluster().sync();   // release/acquire over the cluster's shared and global writes
-}
-
-template <class T, int C>
-__global__ void __launch_bounds__(NARROW_THREADS) k_sweep_fwd_narrow(Dev d) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ring = (T*)smem_raw;
-  FwdRec<T>* stage = (FwdRec<T>*)(smem_raw + (size_t)13 * RING * sizeof(T));
-  FwdRec<T>* st = stage + threadIdx.x;               // staged record of this thread's next position
-  const int s = d.g_solve0 + blockIdx.x / C, r = blockIdx.x % C;  // one cluster of C blocks per solve
-  if (d.st[s].state != 0 || d.flow[s].scheme == 1) return;   // uniform over the cluster
-  if constexpr (C > 1) cg::this_cluster().sync();    // every block runs before any remote read
-  const bool sa_on = d.flow[s].sa_on;
-  const int l0 = d.lvl_solve_ptr[s], l1 = d.lvl_solve_ptr[s + 1] - 1;
-  const int pbase = d.fwd_lvl[l0];
-  const int step = C * (int)blockDim.x;
-  // level bounds travel in registers: level l spans [b, e), the next one [e, en)
-  int b = d.fwd_lvl[l0], e = d.fwd_lvl[l0 + 1];
-  int pm = first_own<C>(b, pbase, r) + C * (int)threadIdx.x;    // this thread's position of the level
-  if (l0 < l1 && pm < e) fwd_stage<T>(d, pm, st);
-  for (int l = l0; l < l1; l++) {
-    const int en = (l + 1 < l1) ? d.fwd_lvl[l + 2] : e;
-    const bool mine = pm < e;
-    FwdRec<T> cur;
-    if (mine) {
-      cpa_wait_all();
-      cur = *st;                 // this level's record into registers, freeing the stage
-    }
-    // the next level's record is in flight while this level is computed
-    const int pn = first_own<C>(e, pbase, r) + C * (int)threadIdx.x;
-    if (pn < en) fwd_stage<T>(d, pn, st);
-    if (mine) fwd_process<T, C>(d, ring, pm, pbase, &cur, sa_on);
-    for (int p = pm + step; p < e; p += step) {   // levels wider than the cluster's threads
-      FwdRec<T> xt;
-      fwd_load_direct<T>(d, p, &xt);
-      fwd_process<T, C>(d, ring, p, pbase, &xt, sa_on);
-    }
-    level_barrier<C>();
-    b = e;
-    e = en;
-    pm = pn;
-  }
-}
-
-// backward record: state (5), 1/D, 1/a_ii, u, v, H, the forward increment dW* (5), cell,
-// entry count and PF_E entries (upper neighbours, wall/symmetry ghosts)
-template <class T>
-struct BwdRec {
-  T w[5], c[5], ws[5];
-  T co[4][PF_E];
-  int i, cnt;
-  int j[PF_E], slot[PF_E];
-};
-
-template <class T>
-__device__ __forceinline__ void bwd_stage(const Dev& d, int p, BwdRec<T>* st) {
-  const int P = d.npos;
-  const T* rec = (const T*)d.rec_b;
-  const T* ec = (const T*)d.ec_b;
-#pragma unroll
-  for (int v = 0; v < 5; v++) {
-    cpa(&st->w[v], rec + v * P + p);
-    cpa(&st->c[v], rec + (5 + v) * P + p);
-    cpa(&st->ws[v], rec + (10 + v) * P + p);
-  }
-  cpa(&st->i, d.bwd_order + p);
-  cpa(&st->cnt, d.cnt_b + p);
-#pragma unroll
-  for (int e = 0; e < PF_E; e++) {
-    cpa(&st->j[e], d.ej_b + e * P + p);
-    cpa(&st->slot[e], d.eslot_b + e * P + p);
-#pragma unroll
-    for (int k = 0; k < 4; k++) cpa(&st->co[k][e], ec + (k * PF_E + e) * P + p);
-  }
-  cpa_commit();
-}
-
-template <class T>
-__device__ __forceinline__ void bwd_load_direct(const Dev& d, int p, BwdRec<T>* st) {
-  const int P = d.npos;
-  const T* rec = (const T*)d.rec_b;
-  const T* ec = (const T*)d.ec_b;
-#pragma unroll
-  for (int v = 0; v < 5; v++) {
-    st->w[v] = rec[v * P + p];
-    st->c[v] = rec[(5 + v) * P + p];
-    st->ws[v] = rec[(10 + v) * P + p];
-  }
-  st->i = d.bwd_order[p];
-  st->cnt = d.cnt_b[p];
-#pragma unroll
-  for (int e = 0; e < PF_E; e++) {
-    st->j[e] = d.ej_b[e * P + p];
-    st->slot[e] = d.eslot_b[e * P + p];
-#pragma unroll
-    for (int k = 0; k < 4; k++) st->co[k][e] = ec[(k * PF_E + e) * P + p];
-  }
-}
-
-// contribution of one backward entry: upper neighbour j (its increments from the ring or
-// global memory), or a wall/symmetry ghost (j = -1 - face: boundary map of this cell's
-// own forward increment ws, flux increment about the ghost state)
-// the increments of a wall / symmetry ghost (face fc) in the backward sweep: the boundary
-// map of the cell's own forward increment ws, and the flux increment about the ghost state
 template <class T>
 __device__ __forceinline__ T mn_x(T a, T fx, T b, T fy) { return fma_x(a, fx, mul_x(b, fy)); }
 
+// the increments of a wall / symmetry ghost (face fc) in the backward sweep: the boundary
+// map of the cell's own forward increment ws, and the flux increment about the ghost state
 template <class T>
 __device__ __forceinline__ void ghost_entry(const Dev& d, int fc, const T* ws, T* f, T* w) {
   const int nf = d.nf;
@@ -698,6 +576,8 @@ __device__ __forceinline__ void ghost_entry(const Dev& d, int fc, const T* ws, T
                 w[0], w[1], w[2], w[3], f);
 }
 
+// contribution of one backward entry: upper neighbour j (its increments from the ring or
+// global memory), or a wall/symmetry ghost (j = -1 - face)
 template <class T, int C>
 __device__ __forceinline__ void bwd_entry(const Dev& d, const T* ring, const T* dF, const T* dWo, int j, int slot,
                                           const T* ws, T sx, T sy, T sl, T sa, bool sa_on, T* acc) {
@@ -708,21 +588,22 @@ __device__ __forceinline__ void bwd_entry(const Dev& d, const T* ring, const T* 
 }
 
 template <class T, int C = 1>
-__device__ __forceinline__ void bwd_process(const Dev& d, T* ring, int p, int pbase, const BwdRec<T>* r, bool sa_on) {
+__device__ __forceinline__ void bwd_process(const Dev& d, T* ring, int p, int pbase, const BwdStat& st,
+                                            const BwdDyn<T>& dy, bool sa_on) {
   const int n = d.nc_pad;
   T* dWo = (T*)d.dW;
   T* dF = (T*)d.dF;
   T ws[5];
 #pragma unroll
-  for (int v = 0; v < 5; v++) ws[v] = r->ws[v];
+  for (int v = 0; v < 5; v++) ws[v] = dy.ws[v];
   T acc[5] = {0, 0, 0, 0, 0};
-  const int cnt = r->cnt;
+  const int cnt = st.cnt;
   if (cnt >= 0) {
 #pragma unroll
     for (int e = 0; e < PF_E; e++) {
       if (e >= cnt) break;
-      bwd_entry<T, C>(d, ring, dF, dWo, r->j[e], r->slot[e], ws, r->co[0][e], r->co[1][e], r->co[2][e],
-                      r->co[3][e], sa_on, acc);
+      bwd_entry<T, C>(d, ring, dF, dWo, st.j[e], st.slot[e], ws, dy.co[0][e], dy.co[1][e], dy.co[2][e],
+                      dy.co[3][e], sa_on, acc);
     }
   } else {
     const T* sc = (const T*)d.sc_b;
@@ -733,375 +614,221 @@ __device__ __forceinline__ void bwd_process(const Dev& d, T* ring, int p, int pb
   }
   T dw[5];
 #pragma unroll
-  for (int v = 0; v < 4; v++) dw[v] = inc_bwd<T>(ws[v], acc[v], r->c[0]);
-  dw[4] = sa_on ? inc_bwd<T>(ws[4], acc[4], r->c[1]) : (T)0;
+  for (int v = 0; v < 4; v++) dw[v] = inc_bwd<T>(ws[v], acc[v], dy.c[0]);
+  dw[4] = sa_on ? inc_bwd<T>(ws[4], acc[4], dy.c[1]) : (T)0;
   T o[8];
-  delta_flux<T>(r->w[0], r->w[1], r->w[2], r->c[2], r->c[3], r->c[4], dw[0], dw[1], dw[2], dw[3], o);
+  delta_flux<T>(dy.w[0], dy.w[1], dy.w[2], dy.c[2], dy.c[3], dy.c[4], dw[0], dw[1], dw[2], dw[3], o);
   ring_put<T>(ring, (p - pbase) % RING, o, dw);
-  const int i = r->i;
+  const int i = st.i;
 #pragma unroll
   for (int v = 0; v < 5; v++) dWo[v * n + i] = dw[v];
 #pragma unroll
   for (int k = 0; k < 8; k++) dF[k * n + i] = o[k];
 }
 
-template <class T, int C>
-__global__ void __launch_bounds__(NARROW_THREADS) k_sweep_bwd_narrow(Dev d) {
+// ---- one block per solve: levels staged by bulk copies NST levels ahead ----
+constexpr int NST = 3;   // stage buffers (levels in flight)
+template <class T>
+__host__ __device__ constexpr int stage_max() { return sizeof(T) == 4 ? 256 : 128; }   // records per stage
+
+template <class T, bool FWD>
+struct Rec {
+  using Stat = typename std::conditional<FWD, FwdStat, BwdStat>::type;
+  using Dyn = typename std::conditional<FWD, FwdDyn<T>, BwdDyn<T>>::type;
+};
+
+// dynamic shared memory: ring | NST x stage_max static records | NST x stage_max dynamic
+// records | NST mbarriers | abort flag
+template <class T, bool FWD>
+__host__ __device__ constexpr size_t stage_stat_off() { return (size_t)13 * RING * sizeof(T); }
+template <class T, bool FWD>
+__host__ __device__ constexpr size_t stage_dyn_off() {
+  return stage_stat_off<T, FWD>() + (size_t)NST * stage_max<T>() * sizeof(typename Rec<T, FWD>::Stat);
+}
+template <class T, bool FWD>
+__host__ __device__ constexpr size_t stage_bar_off() {
+  return stage_dyn_off<T, FWD>() + (size_t)NST * stage_max<T>() * sizeof(typename Rec<T, FWD>::Dyn);
+}
+template <class T, bool FWD>
+__host__ __device__ constexpr size_t bulk_smem() { return stage_bar_off<T, FWD>() + 8 * NST + 16; }
+
+// issue the bulk copies of level [b, e) (its first stage_max records) into stage k
+template <class T, bool FWD>
+__device__ __forceinline__ void stage_level(const Dev& d, unsigned char* smem, int k, int b, int e) {
+  using Stat = typename Rec<T, FWD>::Stat;
+  using Dyn = typename Rec<T, FWD>::Dyn;
+  const int nrec = min(e - b, stage_max<T>());
+  const unsigned bar = (unsigned)__cvta_generic_to_shared(smem + stage_bar_off<T, FWD>() + 8 * k);
+  const unsigned ss = (unsigned)__cvta_generic_to_shared(smem + stage_stat_off<T, FWD>()) +
+                      (unsigned)(k * stage_max<T>() * sizeof(Stat));
+  const unsigned sd = (unsigned)__cvta_generic_to_shared(smem + stage_dyn_off<T, FWD>()) +
+                      (unsigned)(k * stage_max<T>() * sizeof(Dyn));
+  const Stat* gs = (FWD ? (const Stat*)d.fst : (const Stat*)d.bst) + b;
+  const Dyn* gd = (const Dyn*)(FWD ? d.fdyn : d.bdyn) + b;
+  mbar_expect(bar, (unsigned)(nrec * (sizeof(Stat) + sizeof(Dyn))));
+  bulk_g2s(ss, gs, (unsigned)(nrec * sizeof(Stat)), bar);
+  bulk_g2s(sd, gd, (unsigned)(nrec * sizeof(Dyn)), bar);
+}
+
+// The sweep of one solve by one block. Level l (k = l - l0) sits in stage k % NST, phase
+// (k / NST) & 1 of its barrier. Thread 0 issues the copies; every thread waits for its
+// level's barrier (at most wait_limit tries: a wait that runs out marks the solve
+// IGKS_TIMEOUT, the block stops after the level barrier, waits for its copies in flight,
+// and the update leaves the solve's state untouched). Positions beyond stage_max of a wide
+// level read their records from global memory.
+template <class T, bool FWD>
+__device__ __forceinline__ void sweep_bulk(const Dev& d) {
+  using Stat = typename Rec<T, FWD>::Stat;
+  using Dyn = typename Rec<T, FWD>::Dyn;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = (T*)smem_raw;
-  BwdRec<T>* stage = (BwdRec<T>*)(smem_raw + (size_t)13 * RING * sizeof(T));
-  BwdRec<T>* st = stage + threadIdx.x;
-  const int s = d.g_solve0 + blockIdx.x / C, r = blockIdx.x % C;
+  const Stat* sst = (const Stat*)(smem_raw + stage_stat_off<T, FWD>());
+  const Dyn* sdy = (const Dyn*)(smem_raw + stage_dyn_off<T, FWD>());
+  const unsigned bar0 = (unsigned)__cvta_generic_to_shared(smem_raw + stage_bar_off<T, FWD>());
+  volatile int* abort_flag = (volatile int*)(smem_raw + stage_bar_off<T, FWD>() + 8 * NST);
+  const int s = d.g_solve0 + blockIdx.x;
   if (d.st[s].state != 0 || d.flow[s].scheme == 1) return;
-  if constexpr (C > 1) cg::this_cluster().sync();
+  if (!FWD && d.tmo[s]) return;                       // the forward sweep of this solve gave up
   const bool sa_on = d.flow[s].sa_on;
-  const int l0 = d.blvl_solve_ptr[s], l1 = d.blvl_solve_ptr[s + 1] - 1;
-  const int pbase = d.bwd_lvl[l0];
+  const int* lvl = FWD ? d.fwd_lvl : d.bwd_lvl;
+  const int* lsp = FWD ? d.lvl_solve_ptr : d.blvl_solve_ptr;
+  const int l0 = lsp[s], l1 = lsp[s + 1] - 1, nl = l1 - l0;
+  if (nl <= 0) return;
+  const Stat* gst = FWD ? (const Stat*)d.fst : (const Stat*)d.bst;
+  const Dyn* gdy = (const Dyn*)(FWD ? d.fdyn : d.bdyn);
+  const int limit = d.wait_limit;
+  const int tid = threadIdx.x;
+  int issued = 0;                                     // levels issued (thread 0)
+  int nb = 0;                                         // offset of the next level to issue (thread 0)
+  if (tid == 0) {
+    for (int k = 0; k < NST; k++) mbar_init(bar0 + 8 * k, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    nb = lvl[l0];
+    for (; issued < NST && issued < nl; issued++) {
+      const int e = lvl[l0 + issued + 1];
+      if (!(FWD && d.starve_test && issued == 1)) stage_level<T, FWD>(d, smem_raw, issued, nb, e);
+      nb = e;
+    }
+  }
+  __syncthreads();
+  const int pbase = lvl[l0];
+  int b = lvl[l0], e = lvl[l0 + 1];
+  int k = 0;
+  for (; k < nl; k++) {
+    const int l = l0 + k;
+    const int en = (k + 1 < nl) ? lvl[l + 2] : e;     // next level's end, loaded a level early
+    const int st_k = k % NST;
+    const int nnext = (tid == 0 && issued < nl) ? lvl[l0 + issued + 1] : 0;   // for the copy issued below
+    const bool mine = b + tid < e;
+    bool ok = true;
+    if (mine) ok = mbar_wait(bar0 + 8 * st_k, (unsigned)((k / NST) & 1), limit);
+    if (!ok) {
+      d.tmo[s] = 1;
+      *abort_flag = 1;
+    } else {
+      const int smax = stage_max<T>();
+      for (int p = b + tid; p < e; p += blockDim.x) {
+        const int q = p - b;
+        const Stat cs = load_rec(q < smax ? sst + st_k * smax + q : gst + p);
+        const Dyn cd = load_rec(q < smax ? sdy + st_k * smax + q : gdy + p);
+        if constexpr (FWD) fwd_process<T>(d, ring, p, pbase, cs, cd, sa_on);
+        else bwd_process<T>(d, ring, p, pbase, cs, cd, sa_on);
+      }
+    }
+    __syncthreads();                                  // level done; stage st_k is free
+    if (*abort_flag) break;
+    if (tid == 0 && issued < nl) {
+      // the stage was read by generic loads: order those before the async proxy's writes
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      stage_level<T, FWD>(d, smem_raw, issued % NST, nb, nnext);
+      nb = nnext;
+      issued++;
+    }
+    b = e;
+    e = en;
+  }
+  // after a wait ran out: let the copies already issued land before the block exits
+  if (tid == 0 && k < nl)
+    for (int kk = k; kk < issued; kk++)
+      if (!(FWD && d.starve_test && kk == 1)) mbar_wait(bar0 + 8 * (kk % NST), (unsigned)((kk / NST) & 1), limit);
+}
+
+template <class T>
+__global__ void __launch_bounds__(NARROW_THREADS) k_sweep_fwd_bulk(Dev d) { sweep_bulk<T, true>(d); }
+template <class T>
+__global__ void __launch_bounds__(NARROW_THREADS) k_sweep_bwd_bulk(Dev d) { sweep_bulk<T, false>(d); }
+
+// ---- a cluster of C blocks per solve: positions dealt round the blocks, records staged
+// per thread with 16-byte cp.async one level ahead ----
+// the first position at or after b that belongs to cluster block r (positions q = p - pbase
+// are dealt round the C blocks: q % C == r)
+template <int C>
+__device__ __forceinline__ int first_own(int b, int pbase, int r) {
+  return b + (((r - (b - pbase)) % C) + C) % C;
+}
+
+template <class T, bool FWD>
+__host__ __device__ constexpr size_t cluster_smem() {
+  return (size_t)13 * RING * sizeof(T) +
+         (size_t)NARROW_THREADS * (sizeof(typename Rec<T, FWD>::Stat) + sizeof(typename Rec<T, FWD>::Dyn));
+}
+
+template <class T, bool FWD, int C>
+__device__ __forceinline__ void sweep_cluster(const Dev& d) {
+  using Stat = typename Rec<T, FWD>::Stat;
+  using Dyn = typename Rec<T, FWD>::Dyn;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ring = (T*)smem_raw;
+  Stat* sst = (Stat*)(smem_raw + (size_t)13 * RING * sizeof(T)) + threadIdx.x;
+  Dyn* sdy = (Dyn*)(smem_raw + (size_t)13 * RING * sizeof(T) + (size_t)NARROW_THREADS * sizeof(Stat)) + threadIdx.x;
+  const int s = d.g_solve0 + blockIdx.x / C, r = blockIdx.x % C;   // one cluster of C blocks per solve
+  if (d.st[s].state != 0 || d.flow[s].scheme == 1) return;         // uniform over the cluster
+  cg::this_cluster().sync();                                       // every block runs before any remote read
+  const bool sa_on = d.flow[s].sa_on;
+  const int* lvl = FWD ? d.fwd_lvl : d.bwd_lvl;
+  const int* lsp = FWD ? d.lvl_solve_ptr : d.blvl_solve_ptr;
+  const int l0 = lsp[s], l1 = lsp[s + 1] - 1;
+  const Stat* gst = FWD ? (const Stat*)d.fst : (const Stat*)d.bst;
+  const Dyn* gdy = (const Dyn*)(FWD ? d.fdyn : d.bdyn);
+  const int pbase = lvl[l0];
   const int step = C * (int)blockDim.x;
-  int b = d.bwd_lvl[l0], e = d.bwd_lvl[l0 + 1];
-  int pm = first_own<C>(b, pbase, r) + C * (int)threadIdx.x;
-  if (l0 < l1 && pm < e) bwd_stage<T>(d, pm, st);
+  int b = lvl[l0], e = lvl[l0 + 1];
+  int pm = first_own<C>(b, pbase, r) + C * (int)threadIdx.x;   // this thread's position of the level
+  if (l0 < l1 && pm < e) { cpa_record(sst, gst + pm); cpa_record(sdy, gdy + pm); cpa_commit(); }
   for (int l = l0; l < l1; l++) {
-    const int en = (l + 1 < l1) ? d.bwd_lvl[l + 2] : e;
+    const int en = (l + 1 < l1) ? lvl[l + 2] : e;
     const bool mine = pm < e;
-    BwdRec<T> cur;
+    Stat cs;
+    Dyn cd;
     if (mine) {
       cpa_wait_all();
-      cur = *st;
+      cs = load_rec(sst);        // this level's record into registers, freeing the stage
+      cd = load_rec(sdy);
     }
     const int pn = first_own<C>(e, pbase, r) + C * (int)threadIdx.x;
-    if (pn < en) bwd_stage<T>(d, pn, st);
-    if (mine) bwd_process<T, C>(d, ring, pm, pbase, &cur, sa_on);
-    for (int p = pm + step; p < e; p += step) {
-      BwdRec<T> xt;
-      bwd_load_direct<T>(d, p, &xt);
-      bwd_process<T, C>(d, ring, p, pbase, &xt, sa_on);
+    if (pn < en) { cpa_record(sst, gst + pn); cpa_record(sdy, gdy + pn); cpa_commit(); }
+    if (mine) {
+      if constexpr (FWD) fwd_process<T, C>(d, ring, pm, pbase, cs, cd, sa_on);
+      else bwd_process<T, C>(d, ring, pm, pbase, cs, cd, sa_on);
     }
-    level_barrier<C>();
+    for (int p = pm + step; p < e; p += step) {   // levels wider than the cluster's threads
+      const Stat xs = load_rec(gst + p);
+      const Dyn xd = load_rec(gdy + p);
+      if constexpr (FWD) fwd_process<T, C>(d, ring, p, pbase, xs, xd, sa_on);
+      else bwd_process<T, C>(d, ring, p, pbase, xs, xd, sa_on);
+    }
+    cg::this_cluster().sync();   // release/acquire over the cluster's shared and global writes
     b = e;
     e = en;
     pm = pn;
   }
 }
 
-
-// ---- narrow schedule with a quad of threads per cell (FP32 and double-float sweeps) ----
-// The four threads of a quad share one cell: thread q accumulates component q (and q = 0
-// the SA row too) over the cell's entries, reading only its own component's three values
-// per neighbour from the ring; the quad then exchanges the four increments by shuffles and
-// each thread forms the flux increment (all eight values, the same function as one thread
-// per cell) and keeps its component's two. The arithmetic of every component is the
-// per-component helpers' in the same entry order, so the iterates are bitwise those of one
-// thread per cell. It shortens the dependent chain of a cell about fourfold where a level
-// holds few cells; it does not pay for FP64, whose cost is the SM's count of FP64 warp
-// instructions (one per ~19 cycles whatever the active lanes), so FP64 keeps one thread
-// per cell.
-constexpr int QUAD = 4;
-
-template <class T>
-__device__ __forceinline__ T shfl_q(T x, int k) { return __shfl_sync(0xffffffffu, x, k, QUAD); }
-template <>
-__device__ __forceinline__ df64 shfl_q<df64>(df64 x, int k) {
-  return df64(__shfl_sync(0xffffffffu, x.hi, k, QUAD), __shfl_sync(0xffffffffu, x.lo, k, QUAD));
-}
-
-// the quad's lanes share the copies of one staged forward record
-template <class T>
-__device__ __forceinline__ void fwd_stage_q(const Dev& d, int p, FwdRec<T>* st, int q) {
-  const int P = d.npos;
-  const T* rec = (const T*)d.rec_f;
-  const T* ec = (const T*)d.ec_f;
-  if (q == 0) {
-#pragma unroll
-    for (int v = 0; v < 5; v++) cpa(&st->m[v], rec + v * P + p);
-    cpa(&st->i, d.fwd_order + p);
-    cpa(&st->cnt, d.cnt_f + p);
-    cpa(&st->pb, d.pb_of_pf + p);
-  } else if (q == 1) {
-#pragma unroll
-    for (int v = 0; v < 3; v++) cpa(&st->w[v], rec + (5 + v) * P + p);
-#pragma unroll
-    for (int v = 0; v < 5; v++) cpa(&st->c[v], rec + (8 + v) * P + p);
-  } else if (q == 2) {
-#pragma unroll
-    for (int e = 0; e < PF_E; e++) {
-      cpa(&st->j[e], d.ej_f + e * P + p);
-      cpa(&st->slot[e], d.eslot_f + e * P + p);
-      cpa(&st->co[0][e], ec + e * P + p);
-    }
-  } else {
-#pragma unroll
-    for (int k = 1; k < 4; k++)
-#pragma unroll
-      for (int e = 0; e < PF_E; e++) cpa(&st->co[k][e], ec + (k * PF_E + e) * P + p);
-  }
-  cpa_commit();
-}
-
-template <class T>
-__device__ __forceinline__ void bwd_stage_q(const Dev& d, int p, BwdRec<T>* st, int q) {
-  const int P = d.npos;
-  const T* rec = (const T*)d.rec_b;
-  const T* ec = (const T*)d.ec_b;
-  if (q == 0) {
-#pragma unroll
-    for (int v = 0; v < 5; v++) cpa(&st->ws[v], rec + (10 + v) * P + p);
-    cpa(&st->i, d.bwd_order + p);
-    cpa(&st->cnt, d.cnt_b + p);
-  } else if (q == 1) {
-#pragma unroll
-    for (int v = 0; v < 5; v++) {
-      cpa(&st->w[v], rec + v * P + p);
-      cpa(&st->c[v], rec + (5 + v) * P + p);
-    }
-  } else if (q == 2) {
-#pragma unroll
-    for (int e = 0; e < PF_E; e++) {
-      cpa(&st->j[e], d.ej_b + e * P + p);
-      cpa(&st->slot[e], d.eslot_b + e * P + p);
-      cpa(&st->co[0][e], ec + e * P + p);
-    }
-  } else {
-#pragma unroll
-    for (int k = 1; k < 4; k++)
-#pragma unroll
-      for (int e = 0; e < PF_E; e++) cpa(&st->co[k][e], ec + (k * PF_E + e) * P + p);
-  }
-  cpa_commit();
-}
-
-// component q of a neighbour's increments: x and y flux increments and the increment (and
-// for q = 0 the SA increment w4)
-template <class T>
-__device__ __forceinline__ void neighbour_q(const Dev& d, const T* ring, const T* dF, const T* dWv, int j, int slot,
-                                            int q, T& f0, T& f1, T& w, T& w4) {
-  const int n = d.nc_pad;
-  if (slot >= 0) {
-    f0 = ring[(2 * q) * RING + slot];
-    f1 = ring[(2 * q + 1) * RING + slot];
-    w = ring[(8 + q) * RING + slot];
-    if (q == 0) w4 = ring[12 * RING + slot];
-  } else {
-    f0 = dF[(2 * q) * n + j];
-    f1 = dF[(2 * q + 1) * n + j];
-    w = dWv[q * n + j];
-    if (q == 0) w4 = dWv[4 * n + j];
-  }
-}
-
-template <class T>
-__device__ __forceinline__ T pick(const T* a, int q) {   // a[q] without local-memory indexing
-  return q == 0 ? a[0] : (q == 1 ? a[1] : (q == 2 ? a[2] : a[3]));
-}
-
-// one forward position processed by a quad; live = the quad holds a position this round
-template <class T>
-__device__ __forceinline__ void fwd_quad(const Dev& d, T* ring, int p, int pbase, const FwdRec<T>& r, int q,
-                                         bool live, bool sa_on) {
-  const int n = d.nc_pad, P = d.npos;
-  T* dWs = (T*)d.dWs;
-  T* dF = (T*)d.dF;
-  T acc = (T)0, acc4 = (T)0;
-  if (live) {
-    acc = pick(r.m, q);
-    acc4 = r.m[4];
-    const int cnt = r.cnt;
-    if (cnt >= 0) {
-#pragma unroll
-      for (int e = 0; e < PF_E; e++) {
-        if (e >= cnt) break;
-        T f0, f1, w, w4;
-        neighbour_q<T>(d, ring, dF, dWs, r.j[e], r.slot[e], q, f0, f1, w, w4);
-        fwd_comp<T>(acc, r.co[0][e], r.co[1][e], r.co[2][e], f0, f1, w);
-        if (q == 0 && sa_on) fwd_sa<T>(acc4, r.co[3][e], w4);
-      }
-    } else {
-      const T* sc = (const T*)d.sc_f;
-      const int nfs = d.nfs;
-      for (int k = d.fs_ptr[p]; k < d.fs_ptr[p + 1]; k++) {
-        T f0, f1, w, w4;
-        neighbour_q<T>(d, ring, dF, dWs, d.fs_j[k], d.fs_slot[k], q, f0, f1, w, w4);
-        fwd_comp<T>(acc, sc[k], sc[nfs + k], sc[2 * nfs + k], f0, f1, w);
-        if (q == 0 && sa_on) fwd_sa<T>(acc4, sc[3 * nfs + k], w4);
-      }
-    }
-  }
-  const T dwq = inc_fwd<T>(acc, r.c[0]);
-  const T dw4 = sa_on ? inc_fwd<T>(acc4, r.c[1]) : (T)0;
-  T dw[4];
-#pragma unroll
-  for (int k = 0; k < 4; k++) dw[k] = shfl_q<T>(dwq, k);   // every lane of the warp takes part
-  if (!live) return;
-  T o[8];
-  delta_flux<T>(r.w[0], r.w[1], r.w[2], r.c[2], r.c[3], r.c[4], dw[0], dw[1], dw[2], dw[3], o);
-  const T o0 = q == 0 ? o[0] : (q == 1 ? o[2] : (q == 2 ? o[4] : o[6]));
-  const T o1 = q == 0 ? o[1] : (q == 1 ? o[3] : (q == 2 ? o[5] : o[7]));
-  const int slot = (p - pbase) % RING;
-  ring[(2 * q) * RING + slot] = o0;
-  ring[(2 * q + 1) * RING + slot] = o1;
-  ring[(8 + q) * RING + slot] = dwq;
-  const int i = r.i, pb = r.pb;
-  T* recb = (T*)d.rec_b;
-  dWs[q * n + i] = dwq;
-  recb[(10 + q) * P + pb] = dwq;            // the backward sweep's copy of dW*
-  dF[(2 * q) * n + i] = o0;
-  dF[(2 * q + 1) * n + i] = o1;
-  if (q == 0) {
-    ring[12 * RING + slot] = dw4;
-    dWs[4 * n + i] = dw4;
-    recb[14 * P + pb] = dw4;
-  }
-}
-
-// component q of one backward entry: an upper neighbour's increments, or a wall / symmetry
-// ghost's (the ghost is formed whole, as with one thread per cell, and component q taken)
-template <class T>
-__device__ __forceinline__ void bwd_entry_q(const Dev& d, const T* ring, const T* dF, const T* dWo, int j, int slot,
-                                            const T* ws, T sx, T sy, T sl, T sa, int q, bool sa_on, T& acc, T& acc4) {
-  T f0, f1, w, w4;
-  if (j >= 0) {
-    neighbour_q<T>(d, ring, dF, dWo, j, slot, q, f0, f1, w, w4);
-  } else {
-    T f[8], wg[5];
-    ghost_entry<T>(d, -1 - j, ws, f, wg);
-    f0 = q == 0 ? f[0] : (q == 1 ? f[2] : (q == 2 ? f[4] : f[6]));
-    f1 = q == 0 ? f[1] : (q == 1 ? f[3] : (q == 2 ? f[5] : f[7]));
-    w = pick(wg, q);
-    w4 = wg[4];
-  }
-  bwd_comp<T>(acc, sx, sy, sl, f0, f1, w);
-  if (q == 0 && sa_on) bwd_sa<T>(acc4, sa, w4);
-}
-
-template <class T>
-__device__ __forceinline__ void bwd_quad(const Dev& d, T* ring, int p, int pbase, const BwdRec<T>& r, int q,
-                                         bool live, bool sa_on) {
-  const int n = d.nc_pad;
-  T* dWo = (T*)d.dW;
-  T* dF = (T*)d.dF;
-  T acc = (T)0, acc4 = (T)0;
-  if (live) {
-    const int cnt = r.cnt;
-    if (cnt >= 0) {
-#pragma unroll
-      for (int e = 0; e < PF_E; e++) {
-        if (e >= cnt) break;
-        bwd_entry_q<T>(d, ring, dF, dWo, r.j[e], r.slot[e], r.ws, r.co[0][e], r.co[1][e], r.co[2][e], r.co[3][e],
-                       q, sa_on, acc, acc4);
-      }
-    } else {
-      const T* sc = (const T*)d.sc_b;
-      const int nbs = d.nbs;
-      for (int k = d.bs_ptr[p]; k < d.bs_ptr[p + 1]; k++)
-        bwd_entry_q<T>(d, ring, dF, dWo, d.bs_j[k], d.bs_slot[k], r.ws, sc[k], sc[nbs + k], sc[2 * nbs + k],
-                       sc[3 * nbs + k], q, sa_on, acc, acc4);
-    }
-  }
-  const T wsq = pick(r.ws, q);
-  const T dwq = inc_bwd<T>(wsq, acc, r.c[0]);
-  const T dw4 = sa_on ? inc_bwd<T>(r.ws[4], acc4, r.c[1]) : (T)0;
-  T dw[4];
-#pragma unroll
-  for (int k = 0; k < 4; k++) dw[k] = shfl_q<T>(dwq, k);
-  if (!live) return;
-  T o[8];
-  delta_flux<T>(r.w[0], r.w[1], r.w[2], r.c[2], r.c[3], r.c[4], dw[0], dw[1], dw[2], dw[3], o);
-  const T o0 = q == 0 ? o[0] : (q == 1 ? o[2] : (q == 2 ? o[4] : o[6]));
-  const T o1 = q == 0 ? o[1] : (q == 1 ? o[3] : (q == 2 ? o[5] : o[7]));
-  const int slot = (p - pbase) % RING;
-  ring[(2 * q) * RING + slot] = o0;
-  ring[(2 * q + 1) * RING + slot] = o1;
-  ring[(8 + q) * RING + slot] = dwq;
-  const int i = r.i;
-  dWo[q * n + i] = dwq;
-  dF[(2 * q) * n + i] = o0;
-  dF[(2 * q + 1) * n + i] = o1;
-  if (q == 0) {
-    ring[12 * RING + slot] = dw4;
-    dWo[4 * n + i] = dw4;
-  }
-}
-
-template <class T>
-__global__ void __launch_bounds__(QUAD_THREADS) k_sweep_fwd_quad(Dev d) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ring = (T*)smem_raw;
-  FwdRec<T>* stage = (FwdRec<T>*)(smem_raw + (size_t)13 * RING * sizeof(T));
-  const int q = threadIdx.x % QUAD, cslot = threadIdx.x / QUAD, ncs = blockDim.x / QUAD;
-  FwdRec<T>* st = stage + cslot;                     // the quad's staged record
-  const int s = d.g_solve0 + blockIdx.x;
-  if (d.st[s].state != 0 || d.flow[s].scheme == 1) return;
-  const bool sa_on = d.flow[s].sa_on;
-  const int l0 = d.lvl_solve_ptr[s], l1 = d.lvl_solve_ptr[s + 1] - 1;
-  const int pbase = d.fwd_lvl[l0];
-  int b = d.fwd_lvl[l0], e = d.fwd_lvl[l0 + 1];
-  int pm = b + cslot;
-  if (l0 < l1 && pm < e) fwd_stage_q<T>(d, pm, st, q);
-  for (int l = l0; l < l1; l++) {
-    const int en = (l + 1 < l1) ? d.fwd_lvl[l + 2] : e;
-    const bool mine = pm < e;
-    FwdRec<T> cur;
-    if (mine) cpa_wait_all();
-    __syncwarp();                     // every lane's copies of the quad's record have landed
-    if (mine) cur = *st;
-    __syncwarp();                     // all lanes have read the stage before it is refilled
-    const int pn = e + cslot;
-    if (pn < en) fwd_stage_q<T>(d, pn, st, q);
-    fwd_quad<T>(d, ring, pm, pbase, cur, q, mine, sa_on);
-    // levels wider than the block's quads: further rounds, records read directly
-    for (int base = b + ncs; base < e; base += ncs) {
-      const int p = base + cslot;
-      const bool live = p < e;
-      FwdRec<T> xt;
-      if (live) fwd_load_direct<T>(d, p, &xt);
-      fwd_quad<T>(d, ring, p, pbase, xt, q, live, sa_on);
-    }
-    __syncthreads();
-    b = e;
-    e = en;
-    pm = pn;
-  }
-}
-
-template <class T>
-__global__ void __launch_bounds__(QUAD_THREADS) k_sweep_bwd_quad(Dev d) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ring = (T*)smem_raw;
-  BwdRec<T>* stage = (BwdRec<T>*)(smem_raw + (size_t)13 * RING * sizeof(T));
-  const int q = threadIdx.x % QUAD, cslot = threadIdx.x / QUAD, ncs = blockDim.x / QUAD;
-  BwdRec<T>* st = stage + cslot;
-  const int s = d.g_solve0 + blockIdx.x;
-  if (d.st[s].state != 0 || d.flow[s].scheme == 1) return;
-  const bool sa_on = d.flow[s].sa_on;
-  const int l0 = d.blvl_solve_ptr[s], l1 = d.blvl_solve_ptr[s + 1] - 1;
-  const int pbase = d.bwd_lvl[l0];
-  int b = d.bwd_lvl[l0], e = d.bwd_lvl[l0 + 1];
-  int pm = b + cslot;
-  if (l0 < l1 && pm < e) bwd_stage_q<T>(d, pm, st, q);
-  for (int l = l0; l < l1; l++) {
-    const int en = (l + 1 < l1) ? d.bwd_lvl[l + 2] : e;
-    const bool mine = pm < e;
-    BwdRec<T> cur;
-    if (mine) cpa_wait_all();
-    __syncwarp();
-    if (mine) cur = *st;
-    __syncwarp();
-    const int pn = e + cslot;
-    if (pn < en) bwd_stage_q<T>(d, pn, st, q);
-    bwd_quad<T>(d, ring, pm, pbase, cur, q, mine, sa_on);
-    for (int base = b + ncs; base < e; base += ncs) {
-      const int p = base + cslot;
-      const bool live = p < e;
-      BwdRec<T> xt;
-      if (live) bwd_load_direct<T>(d, p, &xt);
-      bwd_quad<T>(d, ring, p, pbase, xt, q, live, sa_on);
-    }
-    __syncthreads();
-    b = e;
-    e = en;
-    pm = pn;
-  }
-}
+template <class T, int C>
+__global__ void __launch_bounds__(NARROW_THREADS) k_sweep_fwd_cluster(Dev d) { sweep_cluster<T, true, C>(d); }
+template <class T, int C>
+__global__ void __launch_bounds__(NARROW_THREADS) k_sweep_bwd_cluster(Dev d) { sweep_cluster<T, false, C>(d); }
 
 // ---- wide schedule: one launch per level, all solves ----
 template <class T>
@@ -1132,45 +859,32 @@ void launch_update(const Dev& d, int precision, cudaStream_t s) {
   else k_update<double><<<d.g_nblk, CELL_BLOCK, 0, s>>>(d);
 }
 
-// dynamic shared memory of the narrow sweeps: the ring plus one staged record per thread
-// (one staged record per thread)
 template <class T>
-static size_t fwd_smem() { return (size_t)13 * RING * sizeof(T) + (size_t)NARROW_THREADS * sizeof(FwdRec<T>); }
-template <class T>
-static size_t bwd_smem() { return (size_t)13 * RING * sizeof(T) + (size_t)NARROW_THREADS * sizeof(BwdRec<T>); }
-
-template <class T, int C>
-static void set_smem() {
-  cudaFuncSetAttribute(k_sweep_fwd_narrow<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<T>());
-  cudaFuncSetAttribute(k_sweep_bwd_narrow<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<T>());
-}
-
-template <class T>
-static void set_smem_quad() {
-  cudaFuncSetAttribute(k_sweep_fwd_quad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<T>());
-  cudaFuncSetAttribute(k_sweep_bwd_quad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<T>());
+static void set_smem_t() {
+  cudaFuncSetAttribute(k_sweep_fwd_bulk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bulk_smem<T, true>());
+  cudaFuncSetAttribute(k_sweep_bwd_bulk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bulk_smem<T, false>());
+  cudaFuncSetAttribute(k_sweep_fwd_cluster<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem<T, true>());
+  cudaFuncSetAttribute(k_sweep_bwd_cluster<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem<T, false>());
+  cudaFuncSetAttribute(k_sweep_fwd_cluster<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem<T, true>());
+  cudaFuncSetAttribute(k_sweep_bwd_cluster<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem<T, false>());
+  cudaFuncSetAttribute(k_sweep_fwd_cluster<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem<T, true>());
+  cudaFuncSetAttribute(k_sweep_bwd_cluster<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem<T, false>());
 }
 
 void setup_sweeps() {
-  set_smem<double, 1>(); set_smem<double, 2>(); set_smem<double, 4>(); set_smem<double, 8>();
-  set_smem<float, 1>(); set_smem<float, 2>(); set_smem<float, 4>(); set_smem<float, 8>();
-  set_smem<df64, 1>(); set_smem<df64, 2>(); set_smem<df64, 4>(); set_smem<df64, 8>();
-  set_smem_quad<float>(); set_smem_quad<df64>();
+  set_smem_t<double>();
+  set_smem_t<float>();
+  set_smem_t<df64>();
 }
 
-// one block per solve (C = 1), or one cluster of C blocks per solve
+// one cluster of C blocks per solve
 template <class T, int C>
-static void launch_narrow(bool fwd, const Dev& d, int threads, cudaStream_t s) {
-  void (*k)(Dev) = fwd ? k_sweep_fwd_narrow<T, C> : k_sweep_bwd_narrow<T, C>;
-  const size_t smem = fwd ? fwd_smem<T>() : bwd_smem<T>();
-  if (C == 1) {
-    k<<<d.g_nsolve, threads, smem, s>>>(d);
-    return;
-  }
+static void launch_cluster(bool fwd, const Dev& d, int threads, cudaStream_t s) {
+  void (*k)(Dev) = fwd ? k_sweep_fwd_cluster<T, C> : k_sweep_bwd_cluster<T, C>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(d.g_nsolve * C));
   cfg.blockDim = dim3((unsigned)threads);
-  cfg.dynamicSmemBytes = smem;
+  cfg.dynamicSmemBytes = fwd ? cluster_smem<T, true>() : cluster_smem<T, false>();
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1184,18 +898,14 @@ static void launch_narrow(bool fwd, const Dev& d, int threads, cudaStream_t s) {
 
 template <class T>
 static void launch_narrow_c(bool fwd, const Dev& d, int threads, cudaStream_t s) {
-  if constexpr (!std::is_same<T, double>::value) {
-    if (d.quad && d.sweep_cluster <= 1) {   // a quad of threads per cell
-      void (*k)(Dev) = fwd ? k_sweep_fwd_quad<T> : k_sweep_bwd_quad<T>;
-      k<<<d.g_nsolve, threads, fwd ? fwd_smem<T>() : bwd_smem<T>(), s>>>(d);
-      return;
-    }
-  }
   switch (d.sweep_cluster) {
-    case 2: launch_narrow<T, 2>(fwd, d, threads, s); break;
-    case 4: launch_narrow<T, 4>(fwd, d, threads, s); break;
-    case 8: launch_narrow<T, 8>(fwd, d, threads, s); break;
-    default: launch_narrow<T, 1>(fwd, d, threads, s); break;
+    case 2: launch_cluster<T, 2>(fwd, d, threads, s); break;
+    case 4: launch_cluster<T, 4>(fwd, d, threads, s); break;
+    case 8: launch_cluster<T, 8>(fwd, d, threads, s); break;
+    default:   // one block per solve
+      if (fwd) k_sweep_fwd_bulk<T><<<d.g_nsolve, threads, bulk_smem<T, true>(), s>>>(d);
+      else k_sweep_bwd_bulk<T><<<d.g_nsolve, threads, bulk_smem<T, false>(), s>>>(d);
+      break;
   }
 }
 

@@ -28,7 +28,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
                 ("check_every", C.c_int32), ("use_graph", C.c_int32), ("sweep_threads", C.c_int32),
                 ("timing", C.c_int32), ("sweep_mode", C.c_int32), ("sweep_cluster", C.c_int32),
-                ("groups", C.c_int32), ("sweep_quad", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("groups", C.c_int32), ("wait_limit", C.c_int32), ("starve_test", C.c_int32),
+                ("reserved", C.c_int32 * 1)]
 
 
 class Flow(C.Structure):
@@ -43,8 +44,7 @@ class Flow(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("sweep_threads", C.c_int32), ("flux_block", C.c_int32), ("sweep_mode", C.c_int32),
-                ("sweep_cluster", C.c_int32), ("ms_per_iter", C.c_float), ("groups", C.c_int32),
-                ("sweep_quad", C.c_int32)]
+                ("sweep_cluster", C.c_int32), ("ms_per_iter", C.c_float), ("groups", C.c_int32)]
 
 
 class Status(C.Structure):
@@ -220,10 +220,11 @@ class Context:
     """One igks_ctx: a set of steady solves resident on one GPU."""
 
     def __init__(self, precision=PREC_FP64, device=0, stream=None, check_every=20, use_graph=1,
-                 sweep_threads=0, timing=0, sweep_mode=0, sweep_cluster=0, groups=0, sweep_quad=0):
+                 sweep_threads=0, timing=0, sweep_mode=0, sweep_cluster=0, groups=0, wait_limit=0,
+                 starve_test=0):
         o = Options(precision=precision, device=device, stream=stream, check_every=check_every,
                     use_graph=use_graph, sweep_threads=sweep_threads, timing=timing, sweep_mode=sweep_mode,
-                    sweep_cluster=sweep_cluster, groups=groups, sweep_quad=sweep_quad)
+                    sweep_cluster=sweep_cluster, groups=groups, wait_limit=wait_limit, starve_test=starve_test)
         h = C.c_void_p()
         rc = lib().igks_create(C.byref(o), C.byref(h))
         if rc:
@@ -260,7 +261,7 @@ class Context:
 
     def iterate(self, max_iters):
         st = (Status * len(self.meshes))()
-        rc = self._check(lib().igks_iterate(self.h, max_iters, st), ok=(OK, CONVERGED, DIVERGED))
+        rc = self._check(lib().igks_iterate(self.h, max_iters, st), ok=(OK, CONVERGED, DIVERGED, TIMEOUT))
         return rc, [s.as_dict() for s in st]
 
     def enqueue(self, n_iters):

@@ -73,12 +73,12 @@ def test_footprint_bound_is_host_only_and_monotone():
     assert 1500 < b / big.n_cells < 2500
 
 
-@pytest.mark.parametrize("bad", [dict(sweep_quad=2), dict(sweep_threads=512), dict(sweep_threads=1024, sweep_quad=1),
+@pytest.mark.parametrize("bad", [dict(wait_limit=-1), dict(starve_test=2), dict(sweep_threads=512),
                                  dict(sweep_threads=100), dict(precision=7), dict(sweep_cluster=3)])
 def test_create_rejects_bad_options_on_the_host(bad):
     """igks_create checks its options before it touches a device (so this runs without a
-    GPU): a quad flag other than 0/1, more than 256 threads per sweep block without quads or
-    512 with them, a block that is not whole warps, an unknown precision or cluster size."""
+    GPU): a negative wait limit, a test hook other than 0/1, more than 256 threads per sweep
+    block, a block that is not whole warps, an unknown precision or cluster size."""
     from paper_1709_00803_gb300 import igks
     o = igks.Options(**bad)
     h = C.c_void_p()

@@ -136,3 +136,32 @@ def test_exactly_zero_residual_converges_with_finite_cfl():
     ctx.set_scalars(sid, {"iter": 7, "cfl": 2345.0, "res_inf_prev": 3.5, "res_l2_first": 1.0, "state": 0})
     rc, st = ctx.iterate(1)
     assert rc == igks.CONVERGED and st[sid]["cfl"] == fl.cfl_max
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_sweep_wait_that_runs_out_reports_timeout(precision):
+    """The one-block-per-solve sweeps wait on an mbarrier for each level's bulk-copied
+    records, at most wait_limit tries. The test hook starve_test makes every forward sweep
+    skip the copy of its second level, so that wait runs out (a barrier nothing completes):
+    the solve stops with IGKS_TIMEOUT after one iteration, its fields as they were before it,
+    the block lets its other copies land before it exits, and the device goes on working (a
+    fresh context iterates the same solve as usual)."""
+    from paper_1709_00803_gb300 import igks
+    m = G.flat_plate_hybrid(nx=24, nq=8, ntri_rows=6, first=1e-4, seed=3)
+    fl = F.turbulent_plate_flow()
+    W0 = F.perturbed_state(m, fl, seed=2)
+    ctx = igks.Context(precision=precision, sweep_mode=1, wait_limit=4096, starve_test=1, check_every=1)
+    sid = ctx.mesh_upload(m); ctx.set_flow(sid, fl); ctx.init_freestream(sid)
+    ctx.set_fields(sid, W0)
+    rc, st = ctx.iterate(3)
+    assert rc == igks.TIMEOUT
+    assert st[sid]["state"] == igks.TIMEOUT and st[sid]["iters"] == 1
+    assert np.array_equal(ctx.get_fields(sid), W0)
+    ctx.destroy()
+    ok = igks.Context(precision=precision, sweep_mode=1, check_every=1)
+    sid = ok.mesh_upload(m); ok.set_flow(sid, fl); ok.init_freestream(sid)
+    ok.set_fields(sid, W0)
+    rc, st = ok.iterate(3)
+    assert rc == igks.OK and st[sid]["state"] == 0 and st[sid]["iters"] == 3
+    assert np.all(np.isfinite(ok.get_fields(sid)))
+    ok.destroy()

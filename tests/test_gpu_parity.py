@@ -386,55 +386,6 @@ def test_groups_of_solves_bitwise_equal_one_group(precision):
                 assert np.array_equal(out[k], ref[k]), f"groups {groups}, solve {k}"
 
 
-@pytest.mark.parametrize("precision", [1, 2])
-def test_quad_sweeps_bitwise_equal_one_thread_per_cell(precision):
-    """A quad of threads per cell in the FP32 and double-float sweeps (thread k of the quad
-    accumulates component k) does the same arithmetic in the same entry order as one thread
-    per cell: the fields are bitwise equal. The cases cover levels wider than the block's
-    quads (several rounds per level), cells with more stencil entries than a staged record
-    holds (the CSR path), wall and symmetry ghosts, and a switch of configuration between
-    runs."""
-    from paper_1709_00803_gb300 import igks
-    cases = [(G.turbulent_plate(), F.turbulent_plate_flow(), 1),
-             (G.mixed_polygons(), F.turbulent_plate_flow(), 2),
-             (G.refined_cavity(16, band=2, permute_seed=11), F.cavity_flow(), 3),
-             (G.laminar_plate(), F.laminar_plate_flow(), 4)]
-    ref = None
-    for threads, quad, switch in ((256, 0, (256, 1)), (256, 1, (128, 0)), (512, 1, (256, 0)), (128, 0, (512, 1))):
-        ctx = igks.Context(precision=precision, sweep_mode=1, sweep_threads=threads, sweep_quad=quad, check_every=4)
-        for m, fl, seed in cases:
-            sid = ctx.mesh_upload(m); ctx.set_flow(sid, fl)
-        for k, (m, fl, seed) in enumerate(cases):
-            ctx.init_freestream(k)
-            ctx.set_fields(k, seeded(m, fl, seed))
-        ctx.iterate(5)
-        ctx.set_launch(dict(sweep_threads=switch[0], flux_block=128, sweep_mode=1, sweep_cluster=1, groups=1,
-                            sweep_quad=switch[1]))
-        ctx.iterate(4)
-        out = [ctx.get_fields(k) for k in range(len(cases))]
-        ctx.destroy()
-        if ref is None:
-            ref = out
-        else:
-            for k in range(len(cases)):
-                assert np.array_equal(out[k], ref[k]), f"threads {threads}, quad {quad}, solve {k}"
-
-
-def test_quad_option_is_ignored_for_fp64_sweeps():
-    """FP64 sweeps keep one thread per cell whatever sweep_quad says (same bits)."""
-    from paper_1709_00803_gb300 import igks
-    m, fl = G.mixed_polygons(), F.turbulent_plate_flow()
-    out = []
-    for quad in (0, 1):
-        ctx = igks.Context(precision=0, sweep_mode=1, sweep_quad=quad)
-        sid = ctx.mesh_upload(m); ctx.set_flow(sid, fl)
-        ctx.init_freestream(sid); ctx.set_fields(sid, seeded(m, fl, 9))
-        ctx.iterate(4)
-        out.append(ctx.get_fields(sid))
-        ctx.destroy()
-    assert np.array_equal(out[0], out[1])
-
-
 def test_residual_history_matches_oracle_norms():
     """The per-iteration residual history kept on the device (Eq. 25's norms) against the
     oracle's norms of the same iterations."""
