@@ -1196,11 +1196,11 @@ int igks_footprint_bytes(int32_t n_nodes, int32_t n_cells, int32_t n_faces, int3
   const int64_t ncp = (int64_t)(n_cells + CELL_ALIGN - 1) / CELL_ALIGN * CELL_ALIGN;
   // (plus 16 KiB of residual history per solve, in the fixed part below)
   // per padded cell: 62 doubles (state, gradients, speeds, increments, cell constants),
-  // the sweep records (2 x 48 B static, 240 + 272 B per iteration), 9 ints (CSR pointers,
+  // the sweep records (2 x 48 B static, 2 x 272 B per iteration), 9 ints (CSR pointers,
   // orders, levels, positions) and 16 B to spare; per CSR entry 60 B (face and node lists, sweep
   // stencil coefficients, maps) + 40 B (one sweep entry); per face 34 doubles + 8 ints; per
   // node 2 doubles; a few hundred bytes per solve
-  *out = 1156 * ncp + 100 * (int64_t)nnz + 304 * (int64_t)n_faces + 16 * (int64_t)n_nodes + 4096 + 16384;
+  *out = 1188 * ncp + 100 * (int64_t)nnz + 304 * (int64_t)n_faces + 16 * (int64_t)n_nodes + 4096 + 16384;
   return IGKS_OK;
 }
 

@@ -41,14 +41,26 @@ struct alignas(16) BwdStat { int i, cnt, pad0, pad1; int j[PF_E], slot[PF_E]; };
 // per-iteration part (T = double, float or double-float): forward: residual M[5], state
 // (r, mx, my), 1/D, 1/a_ii, u, v, H and per entry (sx, sy, s lambda, SA coefficient);
 // backward: state W[5], the same five constants, the forward increment dW*[5], entries.
-// Every record is an odd number of 16-byte chunks, so a warp reading its lanes' records
-// from shared memory with 16-byte loads hits distinct banks.
+// The head (up to the entries) and each entry's four coefficients are whole 16-byte
+// chunks, so the pre-pass writes them with vector stores; every record is an odd number
+// of chunks, so a warp reading its lanes' records from shared memory with 16-byte loads
+// hits distinct banks.
 template <class T>
-struct alignas(16) FwdDyn { T m[5], w[3], c[5]; T co[4][PF_E]; T pad[sizeof(T) == 4 ? 7 : 1]; };
+struct alignas(16) FwdDyn {
+  T m[5], w[3], c[5];
+  T pad0[sizeof(T) == 4 ? 3 : 1];
+  T co[PF_E][4];
+  T pad1[4];
+};
 template <class T>
-struct alignas(16) BwdDyn { T w[5], c[5], ws[5]; T co[4][PF_E]; T pad[sizeof(T) == 4 ? 5 : 3]; };
+struct alignas(16) BwdDyn {
+  T w[5], c[5], ws[5];
+  T pad0[1];
+  T co[PF_E][4];
+  T pad1[sizeof(T) == 4 ? 4 : 2];
+};
 static_assert(sizeof(FwdStat) == 48 && sizeof(BwdStat) == 48, "static record size");
-static_assert(sizeof(FwdDyn<float>) == 144 && sizeof(FwdDyn<double>) == 240, "forward record size");
+static_assert(sizeof(FwdDyn<float>) == 144 && sizeof(FwdDyn<double>) == 272, "forward record size");
 static_assert(sizeof(BwdDyn<float>) == 144 && sizeof(BwdDyn<double>) == 272, "backward record size");
 
 struct SolveState {

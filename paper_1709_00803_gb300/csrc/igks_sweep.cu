@@ -21,6 +21,8 @@
 #include <cooperative_groups.h>
 #include <float.h>
 
+#include <cstddef>
+
 #include <type_traits>
 
 #include "igks_df64.cuh"
@@ -168,6 +170,15 @@ __device__ __forceinline__ void fwd_sa<df64>(df64& a, df64 sa, df64 w) { df_mac(
 template <>
 __device__ __forceinline__ void bwd_sa<df64>(df64& a, df64 sa, df64 w) { df_mac(a, sa, w); }
 
+// the first BYTES bytes of src to dst (both 16-byte aligned) as 16-byte stores
+template <size_t BYTES>
+__device__ __forceinline__ void store_chunks(void* dst, const void* src) {
+  static_assert(BYTES % 16 == 0, "whole chunks");
+#pragma unroll
+  for (int k = 0; k < (int)(BYTES / 16); k++)
+    reinterpret_cast<uint4*>(dst)[k] = reinterpret_cast<const uint4*>(src)[k];
+}
+
 // ---- pre-pass: per-cell constants and the signed stencil of every cell ----
 template <class T>
 __global__ void __launch_bounds__(CELL_BLOCK) k_sweep_prep(Dev d) {
@@ -195,19 +206,26 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_sweep_prep(Dev d) {
 #pragma unroll
     for (int q = 0; q < 5; q++) c[q * n + i] = cc[q];
   }
-  // position-ordered records of the narrow schedule
+  // position-ordered records of the narrow schedule: the heads as whole 16-byte chunks
+  // (the backward head's dW* slots are written by the forward sweep afterwards)
   const int pf = d.pos_f[i], pb = d.pos_b[i];
   FwdDyn<T>* rf = (FwdDyn<T>*)d.fdyn + pf;
   BwdDyn<T>* rb = (BwdDyn<T>*)d.bdyn + pb;
   const bool csr_f = d.fst[pf].cnt < 0, csr_b = d.bst[pb].cnt < 0;   // more entries than a record holds
   if (!wide) {
+    FwdDyn<T> hf;
+    BwdDyn<T> hb;
 #pragma unroll
-    for (int q = 0; q < 5; q++) rf->m[q] = (T)d.M[q * n + i];
-    rf->w[0] = (T)r; rf->w[1] = (T)mx; rf->w[2] = (T)my;
+    for (int q = 0; q < 5; q++) hf.m[q] = (T)d.M[q * n + i];
+    hf.w[0] = (T)r; hf.w[1] = (T)mx; hf.w[2] = (T)my;
 #pragma unroll
-    for (int q = 0; q < 5; q++) { rf->c[q] = cc[q]; rb->c[q] = cc[q]; }
+    for (int q = 0; q < 5; q++) { hf.c[q] = cc[q]; hb.c[q] = cc[q]; hb.ws[q] = (T)0; }
 #pragma unroll
-    for (int q = 0; q < 5; q++) rb->w[q] = (T)d.W[q * n + i];
+    for (int q = 0; q < 5; q++) hb.w[q] = (T)d.W[q * n + i];
+    for (int q = 0; q < (int)(sizeof(hf.pad0) / sizeof(T)); q++) hf.pad0[q] = (T)0;
+    hb.pad0[0] = (T)0;
+    store_chunks<offsetof(FwdDyn<T>, co)>(rf, &hf);
+    store_chunks<offsetof(BwdDyn<T>, co)>(rb, &hb);
   }
   T* sc = (T*)d.sw_st;
   const int nnz = d.nnz;
@@ -235,16 +253,9 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_sweep_prep(Dev d) {
         o[eb] = e0; o[d.nbs + eb] = e1; o[2 * d.nbs + eb] = e2; o[3 * d.nbs + eb] = e3;
       }
       const int xf = d.cf_to_ef[k], xb = d.cf_to_eb[k];   // record entry: position * PF_E + e
-      if (xf >= 0) {
-        T (*co)[PF_E] = ((FwdDyn<T>*)d.fdyn)[xf / PF_E].co;
-        const int e = xf % PF_E;
-        co[0][e] = e0; co[1][e] = e1; co[2][e] = e2; co[3][e] = e3;
-      }
-      if (xb >= 0) {
-        T (*co)[PF_E] = ((BwdDyn<T>*)d.bdyn)[xb / PF_E].co;
-        const int e = xb % PF_E;
-        co[0][e] = e0; co[1][e] = e1; co[2][e] = e2; co[3][e] = e3;
-      }
+      alignas(16) const T ent[4] = {e0, e1, e2, e3};      // one entry: whole 16-byte chunks
+      if (xf >= 0) store_chunks<sizeof(ent)>(((FwdDyn<T>*)d.fdyn)[xf / PF_E].co[xf % PF_E], ent);
+      if (xb >= 0) store_chunks<sizeof(ent)>(((BwdDyn<T>*)d.bdyn)[xb / PF_E].co[xb % PF_E], ent);
     }
     // the ghost state of a wall or symmetry face in the form the backward sweep's flux
     // increment takes it (its only ghost entries), so the sweep itself does no FP64 work
@@ -452,6 +463,34 @@ __device__ __forceinline__ void neighbour(const Dev& d, const T* ring, const T* 
   }
 }
 
+// The increments of a record's PF_E entries. The ring reads of all entries are issued
+// together, unconditionally (an unused entry or one whose neighbour left the ring reads a
+// valid slot and its values are not used), so a cell waits for shared memory once rather
+// than once per entry; the rare neighbours that left the ring are then read from global
+// memory. Entries e >= cnt are not applied by the caller.
+template <class T, int C = 1>
+__device__ __forceinline__ void gather_entries(const Dev& d, const T* ring, const T* dF, const T* dWv, const int* j,
+                                               const int* slot, int cnt, T (*f)[8], T (*w)[5]) {
+#pragma unroll
+  for (int e = 0; e < PF_E; e++) {
+    const int sl = slot[e] >= 0 ? slot[e] : 0;
+    const T* rb = ring_of<T, C>(ring, sl);
+#pragma unroll
+    for (int k = 0; k < 8; k++) f[e][k] = rb[k * RING + sl];
+#pragma unroll
+    for (int v = 0; v < 5; v++) w[e][v] = rb[(8 + v) * RING + sl];
+  }
+  const int n = d.nc_pad;
+#pragma unroll
+  for (int e = 0; e < PF_E; e++)
+    if (e < cnt && slot[e] < 0 && j[e] >= 0) {
+#pragma unroll
+      for (int k = 0; k < 8; k++) f[e][k] = dF[k * n + j[e]];
+#pragma unroll
+      for (int v = 0; v < 5; v++) w[e][v] = dWv[v * n + j[e]];
+    }
+}
+
 static_assert(sizeof(FwdDyn<df64>) == sizeof(FwdDyn<double>) && sizeof(BwdDyn<df64>) == sizeof(BwdDyn<double>),
               "double-float records");
 
@@ -519,13 +558,11 @@ __device__ __forceinline__ void fwd_process(const Dev& d, T* ring, int p, int pb
   for (int v = 0; v < 5; v++) acc[v] = dy.m[v];
   const int cnt = st.cnt;
   if (cnt >= 0) {
+    T f[PF_E][8], w[PF_E][5];
+    gather_entries<T, C>(d, ring, dF, dWs, st.j, st.slot, cnt, f, w);
 #pragma unroll
-    for (int e = 0; e < PF_E; e++) {
-      if (e >= cnt) break;
-      T f[8], w[5];
-      neighbour<T, C>(d, ring, dF, dWs, st.j[e], st.slot[e], f, w);
-      fwd_acc<T>(acc, dy.co[0][e], dy.co[1][e], dy.co[2][e], dy.co[3][e], f, w, sa_on);
-    }
+    for (int e = 0; e < PF_E; e++)
+      if (e < cnt) fwd_acc<T>(acc, dy.co[e][0], dy.co[e][1], dy.co[e][2], dy.co[e][3], f[e], w[e], sa_on);
   } else {
     // more entries than the record holds: the position-ordered CSR stencil
     const T* sc = (const T*)d.sc_f;
@@ -599,12 +636,14 @@ __device__ __forceinline__ void bwd_process(const Dev& d, T* ring, int p, int pb
   T acc[5] = {0, 0, 0, 0, 0};
   const int cnt = st.cnt;
   if (cnt >= 0) {
+    T f[PF_E][8], w[PF_E][5];
+    gather_entries<T, C>(d, ring, dF, dWo, st.j, st.slot, cnt, f, w);
 #pragma unroll
-    for (int e = 0; e < PF_E; e++) {
-      if (e >= cnt) break;
-      bwd_entry<T, C>(d, ring, dF, dWo, st.j[e], st.slot[e], ws, dy.co[0][e], dy.co[1][e], dy.co[2][e],
-                      dy.co[3][e], sa_on, acc);
-    }
+    for (int e = 0; e < PF_E; e++)
+      if (e < cnt && st.j[e] < 0) ghost_entry<T>(d, -1 - st.j[e], ws, f[e], w[e]);   // wall / symmetry ghost
+#pragma unroll
+    for (int e = 0; e < PF_E; e++)
+      if (e < cnt) bwd_acc<T>(acc, dy.co[e][0], dy.co[e][1], dy.co[e][2], dy.co[e][3], f[e], w[e], sa_on);
   } else {
     const T* sc = (const T*)d.sc_b;
     const int nbs = d.nbs;
@@ -730,8 +769,15 @@ __device__ __forceinline__ void sweep_bulk(const Dev& d) {
       const int smax = stage_max<T>();
       for (int p = b + tid; p < e; p += blockDim.x) {
         const int q = p - b;
-        const Stat cs = load_rec(q < smax ? sst + st_k * smax + q : gst + p);
-        const Dyn cd = load_rec(q < smax ? sdy + st_k * smax + q : gdy + p);
+        Stat cs;
+        Dyn cd;
+        if (q < smax) {              // staged: shared-memory loads
+          cs = load_rec(sst + st_k * smax + q);
+          cd = load_rec(sdy + st_k * smax + q);
+        } else {
+          cs = load_rec(gst + p);
+          cd = load_rec(gdy + p);
+        }
         if constexpr (FWD) fwd_process<T>(d, ring, p, pbase, cs, cd, sa_on);
         else bwd_process<T>(d, ring, p, pbase, cs, cd, sa_on);
       }
