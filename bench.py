@@ -63,10 +63,11 @@ FLUX_ALG_FLOPS_PER_FACE = 2000.0
 NCU = {
     "naca_batch": {"source": "ncu, k_flux on an 8-airfoil slice of the 64-airfoil batch",
                    "flux_exec_flops_per_face": None, "flux_dram_bytes_per_face": None},
-    "turbulent_plate": {"source": "ncu, k_flux and the narrow sweeps on the turbulent flat plate (35056 faces)",
-                        "flux_exec_flops_per_face": 3122.0, "flux_dram_bytes_per_face": 188.1,
-                        "sweep_dram_bytes_per_cell": {("k_sweep_fwd", 8): 279.1, ("k_sweep_bwd", 8): 296.2,
-                                                      ("k_sweep_fwd", 4): 162.7, ("k_sweep_bwd", 4): 170.4}},
+    "turbulent_plate": {"source": "ncu, k_flux and the one-block-per-solve sweeps on the turbulent flat plate "
+                                  "(35056 faces, 20480 cells)",
+                        "flux_exec_flops_per_face": 2231.0, "flux_dram_bytes_per_face": 186.9,
+                        "sweep_dram_bytes_per_cell": {("k_sweep_fwd", 8): 326.2, ("k_sweep_bwd", 8): 326.7,
+                                                      ("k_sweep_fwd", 4): 194.3, ("k_sweep_bwd", 4): 197.7}},
 }
 
 
@@ -79,9 +80,12 @@ def alg_bytes(kernel, t, nc, nf):
         "k_gradient": nc * (5 * 8 + 2 * 8 + 8 + 8 * 8 + 4 * 8 + 8 + 8) + nf * (2 * 4 + 8 + 8),
         "k_flux": nf * (4 * 4 + 8 * 8 + 10 * 8) + nc * cell_flux_inputs,
         "k_residual": nc * (8 + 8 * 8 + 5 * 8 + 3 * 8) + nf * (6 * 8 + 4 * 8),
-        "k_sweep_fwd": nc * (13 * t + 3 * 4 + 4 * (2 * 4 + 4 * t) + 18 * t),
-        "k_sweep_bwd": nc * (15 * t + 2 * 4 + 4 * (2 * 4 + 4 * t) + 13 * t),
-        "k_sweep_prep": nc * (5 * 8 + 8 + 8 + 23 * t) + nf * (6 * 8),
+        # records in (48 B static; 13 + 16 T forward, 15 + 16 T backward), increments out
+        "k_sweep_fwd": nc * (48 + 29 * t + 18 * t),
+        "k_sweep_bwd": nc * (48 + 31 * t + 13 * t),
+        # W, M, Lambda, velocity, SA diagonal in; record heads (13 + 15 T) and about four
+        # stencil entries of 4 T out; face geometry and spectral radius
+        "k_sweep_prep": nc * (2 * 5 * 8 + 8 + 2 * 8 + 8 + 28 * t + 16 * t) + nf * (6 * 8),
     }
     return per.get(kernel)
 

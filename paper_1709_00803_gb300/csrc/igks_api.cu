@@ -1106,7 +1106,7 @@ int igks_autotune(igks_ctx* ctx, int32_t iters_per_trial, igks_tuning* out) {
   const int flux_blocks[] = {64, 128};
   const int sweep_threads[] = {128, 256};
   const int clusters[] = {1, 2, 4};
-  const int groups[] = {1, 2, 4};
+  const int groups[] = {1, 2, 4, 8};
   int err = 0;
   for (int wide = 0; wide <= (wide_ok ? 1 : 0) && !err; wide++)
     for (int fb : flux_blocks)
