@@ -61,8 +61,8 @@ FLUX_ALG_FLOPS_PER_FACE = 2000.0
 # from (executed FP64 flops = 2 x DFMA + DADD + DMUL thread instructions; DRAM = read +
 # write bytes). None: not captured for that workload.
 NCU = {
-    "naca_batch": {"source": "ncu, k_flux on an 8-airfoil slice of the 64-airfoil batch",
-                   "flux_exec_flops_per_face": None, "flux_dram_bytes_per_face": None},
+    "naca_batch": {"source": "ncu, k_flux on the first 8 airfoils of the batch (573454 faces), per face",
+                   "flux_exec_flops_per_face": 2230.7, "flux_dram_bytes_per_face": 220.6},
     "turbulent_plate": {"source": "ncu, k_flux and the one-block-per-solve sweeps on the turbulent flat plate "
                                   "(35056 faces, 20480 cells)",
                         "flux_exec_flops_per_face": 2231.0, "flux_dram_bytes_per_face": 186.9,
@@ -393,23 +393,21 @@ def measure_batch(args, cases, precision, dev, dist, ws, with_e2e=False):
            "diverged": sum(1 for x in states if x < 0), "live_cells_first_last": [live0, int(ncells[np.array([x == 0 for x in states])].sum())],
            "autotune": tuning}
     if with_e2e:
-        # every solve's state in from pinned host memory, one iteration through the public
-        # API (igks_iterate reads the per-solve status back), every state out again
-        hosts = [torch.empty((5, m.n_cells), dtype=torch.float64).pin_memory().numpy() for m, _ in cases]
-        for k, h in enumerate(hosts):
-            ctx.get_fields(k, out=h)
+        # every solve's state in from pinned host memory (igks_set_fields_all: one copy per
+        # solve, checked on the device), one iteration through the public API (igks_iterate
+        # reads the per-solve status back), every state out again (igks_get_fields_all)
+        host = torch.empty((5, int(ncells.sum())), dtype=torch.float64).pin_memory().numpy()
+        ctx.get_fields_all(out=host)
         n_e2e = max(3, min(args.steps, 10))
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
-            for k, h in enumerate(hosts):
-                ctx.set_fields(k, h)
+            ctx.set_fields_all(host)
             _, st = ctx.iterate(1)
-            for k, h in enumerate(hosts):
-                ctx.get_fields(k, out=h)
+            ctx.get_fields_all(out=host)
         e2e_s = _max_over_ranks(dist, time.perf_counter() - t0, f"cuda:{dev}")
-        nbytes = int(sum(h.nbytes for h in hosts))
+        nbytes = int(host.nbytes)
         res["e2e"] = {"value": ws * int(ncells.sum()) * n_e2e / e2e_s, "unit": METRIC,
                       "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 48 * len(cases),
                       "steps": n_e2e}
@@ -671,11 +669,13 @@ def main_batch(args):
     out = {"metric": METRIC, "value": head["value"], "unit": METRIC, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if precision == "fp64" else "f64 flux/residual/update + f32 sweeps",
+           "dtype": {"fp64": "f64", "df64": "f64 flux/residual/update + double-float (2 x f32) sweeps"}.get(
+               precision, "f64 flux/residual/update + f32 sweeps"),
            "data": "synthetic",
            "config": {"workload": desc, "solves": len(cases), "cells": tot.n_cells, "faces": tot.n_faces,
                       "precision": precision, "parallelism": "replicas" if ws > 1 else "one context, all solves",
-                      "l2": "not flushed: the state and mesh data of a step (over 2 GB) exceed the 129 MB L2",
+                      "l2": "not flushed: the state and mesh data of a step (%.1f GB) exceed the 129 MB L2"
+                            % (sum(igks.footprint_bytes(m) for m, _ in cases) / 1e9),
                       "timing": "one window of --steps iterations between CUDA events on the library stream"},
            "e2e": head["e2e"], "gpu_launches": head["launches_per_step"] * args.steps,
            "kernel_ms": head["kernel_ms"], "roofline": dominant, "roofline_flux": flux_roof,

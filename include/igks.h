@@ -182,6 +182,18 @@ int igks_get_fields(igks_ctx* ctx, int32_t solve, double* W);
  * igks_set_scalars is called too. */
 int igks_set_fields(igks_ctx* ctx, int32_t solve, const double* W);
 
+/* The state of every solve at once (checkpoint / restore of a whole context, and the
+ * host round trip of a batched step): W[5 * N] SoA with N the summed cell counts, each
+ * variable's block holding the solves in upload order, a solve's cells contiguous
+ * (solve k starts at the sum of the cell counts before it). One asynchronous copy per
+ * solve on the context stream and one synchronisation. igks_set_fields_all checks each
+ * solve's state on the device (density positive, energy finite) and writes only the solves
+ * that pass; if any fails it returns IGKS_EINVAL and those solves keep their state. It
+ * uses the backward-sweep increment buffer as staging (scratch between iterations).
+ * Errors: IGKS_EINVAL, IGKS_ECUDA. */
+int igks_get_fields_all(igks_ctx* ctx, double* W);
+int igks_set_fields_all(igks_ctx* ctx, const double* W);
+
 /* Iteration scalars of a solve, for checkpoint/resume: out[0] iteration count,
  * out[1] CFL, out[2] previous max|M_rho|, out[3] first-iteration L2 residual,
  * out[4] state. igks_set_scalars takes the same layout. */

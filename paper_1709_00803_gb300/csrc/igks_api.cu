@@ -60,6 +60,11 @@ struct igks_ctx {
   std::vector<cudaStream_t> gstream;
   std::vector<cudaGraph_t> ggraph;
   std::vector<cudaGraphExec_t> ggexec;
+  // the whole batch for check_every iterations as one graph: every group's chain of
+  // iterations as a branch between a fork and a join (one launch per status check)
+  cudaGraph_t bgraph = nullptr;
+  cudaGraphExec_t bexec = nullptr;
+  int bgraph_iters = 0;
   std::vector<std::vector<cudaEvent_t>> gev;
   std::vector<cudaEvent_t> join_ev;
   cudaEvent_t fork_ev = nullptr;
@@ -151,6 +156,11 @@ static int upload(igks_ctx* ctx, const T** out, const std::vector<T>& h) {
 // the per-group streams, graphs and events (group 0's stream is the context stream when
 // there is one group)
 static void release_groups(igks_ctx* ctx) {
+  if (ctx->bexec) cudaGraphExecDestroy(ctx->bexec);
+  if (ctx->bgraph) cudaGraphDestroy(ctx->bgraph);
+  ctx->bexec = nullptr;
+  ctx->bgraph = nullptr;
+  ctx->bgraph_iters = 0;
   for (auto& g : ctx->ggexec) if (g) cudaGraphExecDestroy(g);
   for (auto& g : ctx->ggraph) if (g) cudaGraphDestroy(g);
   ctx->ggexec.clear();
@@ -268,6 +278,28 @@ static int setup_groups(igks_ctx* ctx) {
       if (e != cudaSuccess) return fail(ctx, IGKS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
       CK(cudaGraphInstantiate(&ctx->ggexec[g], ctx->ggraph[g], 0));
     }
+    // the batch graph: check_every iterations of every group, the groups' chains running
+    // side by side (a group may run ahead of another inside it, as with the per-group
+    // launches); not with per-kernel timing, whose events must stay one per kernel
+    const int R = ctx->opt.check_every;
+    if (!ctx->opt.timing && R >= 2 && R <= MAX_BATCH_GRAPH_ITERS) {
+      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      if (G > 1) {
+        cudaEventRecord(ctx->fork_ev, ctx->stream);
+        for (int g = 0; g < G; g++) cudaStreamWaitEvent(ctx->gstream[g], ctx->fork_ev, 0);
+      }
+      for (int g = 0; g < G; g++)
+        for (int r = 0; r < R; r++) enqueue_iteration(ctx, g);
+      if (G > 1)
+        for (int g = 0; g < G; g++) {
+          cudaEventRecord(ctx->join_ev[g], ctx->gstream[g]);
+          cudaStreamWaitEvent(ctx->stream, ctx->join_ev[g], 0);
+        }
+      cudaError_t e = cudaStreamEndCapture(ctx->stream, &ctx->bgraph);
+      if (e != cudaSuccess) return fail(ctx, IGKS_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
+      CK(cudaGraphInstantiate(&ctx->bexec, ctx->bgraph, 0));
+      ctx->bgraph_iters = R;
+    }
   }
   return 0;
 }
@@ -276,6 +308,12 @@ static int setup_groups(igks_ctx* ctx) {
 // and before whatever the caller puts on it next
 static int run_iterations(igks_ctx* ctx, int n) {
   const int G = ctx->n_groups;
+  for (; ctx->bexec && n >= ctx->bgraph_iters; n -= ctx->bgraph_iters)   // whole check intervals
+    CK(cudaGraphLaunch(ctx->bexec, ctx->stream));
+  if (n == 0) {
+    CK(cudaGetLastError());
+    return 0;
+  }
   if (G > 1) {
     CK(cudaEventRecord(ctx->fork_ev, ctx->stream));
     for (int g = 0; g < G; g++) CK(cudaStreamWaitEvent(ctx->gstream[g], ctx->fork_ev, 0));
@@ -875,6 +913,51 @@ int igks_set_fields(igks_ctx* ctx, int32_t solve, const double* W) {
   CK(h2d_2d(ctx, ctx->dev.W + ctx->cell_off[solve], sizeof(double) * ctx->nc_pad, W, sizeof(double) * n,
             sizeof(double) * n, 5));
   CK(cudaStreamSynchronize(ctx->stream));
+  return IGKS_OK;
+}
+
+int igks_get_fields_all(igks_ctx* ctx, double* W) {
+  if (!ctx || !W || ctx->meshes.empty()) return IGKS_EINVAL;
+  int rc = build(ctx);
+  if (rc) return rc;
+  size_t N = 0;
+  for (const HostMesh& m : ctx->meshes) N += m.nc;
+  size_t off = 0;
+  for (size_t k = 0; k < ctx->meshes.size(); k++) {
+    const size_t n = ctx->meshes[k].nc;
+    CK(cudaMemcpy2DAsync(W + off, sizeof(double) * N, ctx->dev.W + ctx->cell_off[k], sizeof(double) * ctx->nc_pad,
+                         sizeof(double) * n, 5, cudaMemcpyDeviceToHost, ctx->stream));
+    off += n;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return IGKS_OK;
+}
+
+int igks_set_fields_all(igks_ctx* ctx, const double* W) {
+  if (!ctx || !W || ctx->meshes.empty()) return IGKS_EINVAL;
+  int rc = build(ctx);
+  if (rc) return rc;
+  Dev& d = ctx->dev;
+  const int ns = d.n_solves;
+  size_t N = 0;
+  for (const HostMesh& m : ctx->meshes) N += m.nc;
+  double* staged = (double*)d.dW;                  // [5][nc_pad] doubles, scratch between iterations
+  size_t off = 0;
+  for (size_t k = 0; k < ctx->meshes.size(); k++) {
+    const size_t n = ctx->meshes[k].nc;
+    CK(cudaMemcpy2DAsync(staged + ctx->cell_off[k], sizeof(double) * ctx->nc_pad, W + off, sizeof(double) * N,
+                         sizeof(double) * n, 5, cudaMemcpyHostToDevice, ctx->stream));
+    off += n;
+  }
+  CK(cudaMemsetAsync(d.bad, 0, sizeof(int) * ns, ctx->stream));
+  launch_set_state(d, staged, d.bad, ctx->stream);
+  CK(cudaGetLastError());
+  std::vector<int> bad(ns, 0);
+  CK(cudaMemcpyAsync(bad.data(), d.bad, sizeof(int) * ns, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemsetAsync(d.bad, 0, sizeof(int) * ns, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int s = 0; s < ns; s++)
+    if (bad[s]) return fail(ctx, IGKS_EINVAL, "non-physical state (solve " + std::to_string(s) + " kept its state)");
   return IGKS_OK;
 }
 

@@ -498,4 +498,34 @@ void launch_end_iter(const Dev& d, cudaStream_t s) {
   k_end_iter<<<(d.g_nsolve + 63) / 64, 64, 0, s>>>(d);
 }
 
+// ===================================================================================
+// whole-context state upload: a staged [5][nc_pad] state is checked per solve (density
+// positive, energy finite) and committed only for the solves that pass
+// ===================================================================================
+
+__global__ void k_check_state(Dev d, const double* src, int* bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.nc_pad) return;
+  const int s = d.cell_solve[i];
+  if (s < 0) return;
+  const int n = d.nc_pad;
+  if (!(src[i] > 0.0) || !isfinite(src[3 * n + i])) atomicOr(bad + s, 1);
+}
+
+__global__ void k_commit_state(Dev d, const double* src, const int* bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.nc_pad) return;
+  const int s = d.cell_solve[i];
+  if (s < 0 || bad[s]) return;
+  const int n = d.nc_pad;
+#pragma unroll
+  for (int v = 0; v < 5; v++) d.W[v * n + i] = src[v * n + i];
+}
+
+void launch_set_state(const Dev& d, const double* staged, int* bad, cudaStream_t s) {
+  const int g = (d.nc_pad + CELL_BLOCK - 1) / CELL_BLOCK;
+  k_check_state<<<g, CELL_BLOCK, 0, s>>>(d, staged, bad);
+  k_commit_state<<<g, CELL_BLOCK, 0, s>>>(d, staged, bad);
+}
+
 }  // namespace igks

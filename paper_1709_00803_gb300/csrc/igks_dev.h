@@ -188,10 +188,14 @@ void launch_sweep_fwd(const Dev& d, int precision, int threads, cudaStream_t s);
 void launch_sweep_bwd(const Dev& d, int precision, int threads, cudaStream_t s);
 void launch_update(const Dev& d, int precision, cudaStream_t s);
 void launch_end_iter(const Dev& d, cudaStream_t s);
+// check a staged [5][nc_pad] state per solve (bad[s] = 1: non-physical) and copy the
+// solves that pass into W
+void launch_set_state(const Dev& d, const double* staged, int* bad, cudaStream_t s);
 constexpr int N_KERNEL_KINDS = 11;   // kernels of one iteration (the wide sweeps launch per level)
 constexpr int RING = 1024;           // shared-memory ring of the narrow sweeps (cells)
 constexpr int NARROW_THREADS = 256;  // block of the narrow sweeps (one thread per cell of a level)
 constexpr int DEFAULT_WAIT_LIMIT = 1 << 24;   // spins of a device wait (about a second)
+constexpr int MAX_BATCH_GRAPH_ITERS = 64;     // iterations captured in one whole-batch graph at most
 constexpr int WIDE_MAX_LEVELS = 64;  // automatic choice: wide schedule up to this many levels
 constexpr int HIST = 1024;           // iterations of residual history kept per solve
 

@@ -109,6 +109,8 @@ def lib():
         L.igks_iterate.argtypes = [vp, i32, P(Status)]
         L.igks_get_fields.argtypes = [vp, i32, dp]
         L.igks_set_fields.argtypes = [vp, i32, dp]
+        L.igks_get_fields_all.argtypes = [vp, dp]
+        L.igks_set_fields_all.argtypes = [vp, dp]
         L.igks_get_scalars.argtypes = [vp, i32, dp]
         L.igks_set_scalars.argtypes = [vp, i32, dp]
         L.igks_get_array.argtypes = [vp, i32, i32, dp]
@@ -295,6 +297,20 @@ class Context:
             W = np.ascontiguousarray(W, dtype=np.float64)
         assert W.shape == (5, self.meshes[solve].n_cells)
         self._check(lib().igks_set_fields(self.h, solve, _dp(W)))
+
+    def get_fields_all(self, out=None):
+        """The state of every solve: [5, N] with the solves' cells side by side in upload order."""
+        shape = (5, sum(m.n_cells for m in self.meshes))
+        W = np.zeros(shape) if out is None else out
+        assert W.shape == shape and W.dtype == np.float64 and W.flags.c_contiguous
+        self._check(lib().igks_get_fields_all(self.h, _dp(W)))
+        return W
+
+    def set_fields_all(self, W):
+        if not (isinstance(W, np.ndarray) and W.dtype == np.float64 and W.flags.c_contiguous):
+            W = np.ascontiguousarray(W, dtype=np.float64)
+        assert W.shape == (5, sum(m.n_cells for m in self.meshes))
+        self._check(lib().igks_set_fields_all(self.h, _dp(W)))
 
     def get_scalars(self, solve):
         o = np.zeros(5)

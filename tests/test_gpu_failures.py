@@ -165,3 +165,50 @@ def test_sweep_wait_that_runs_out_reports_timeout(precision):
     assert rc == igks.OK and st[sid]["state"] == 0 and st[sid]["iters"] == 3
     assert np.all(np.isfinite(ok.get_fields(sid)))
     ok.destroy()
+
+
+def test_whole_context_state_round_trip_and_rejection():
+    """igks_get_fields_all / igks_set_fields_all move every solve's state in one call: the
+    round trip equals the per-solve calls bitwise, iterating from a state set all at once
+    equals iterating from the same state set solve by solve, and a solve with a
+    non-physical state (negative density) is rejected with IGKS_EINVAL and keeps its state
+    while the other solves take theirs."""
+    from paper_1709_00803_gb300 import igks
+    cases = [(G.flat_plate_hybrid(nx=24, nq=8, ntri_rows=6, first=1e-4, seed=3), F.turbulent_plate_flow(), 2),
+             (G.laminar_plate(), F.laminar_plate_flow(), 5),
+             (G.mixed_polygons(), F.turbulent_plate_flow(), 7)]
+    ctxs = []
+    for _ in range(2):
+        ctx = igks.Context(precision=1, check_every=2)
+        for m, fl, _ in cases:
+            sid = ctx.mesh_upload(m); ctx.set_flow(sid, fl)
+        for k in range(len(cases)):
+            ctx.init_freestream(k)
+        ctxs.append(ctx)
+    a, b = ctxs
+    states = [F.perturbed_state(m, fl, seed=sd) for m, fl, sd in cases]
+    for k, W in enumerate(states):
+        a.set_fields(k, W)
+    b.set_fields_all(np.concatenate(states, axis=1))
+    assert np.array_equal(b.get_fields_all(), np.concatenate([a.get_fields(k) for k in range(len(cases))], axis=1))
+    a.iterate(4); b.iterate(4)
+    got = b.get_fields_all()
+    off = 0
+    for k, (m, _, _) in enumerate(cases):
+        assert np.array_equal(got[:, off:off + m.n_cells], a.get_fields(k))
+        off += m.n_cells
+    # reject one non-physical solve, apply the others
+    before = b.get_fields_all()
+    bad = np.concatenate(states, axis=1)
+    n0 = cases[0][0].n_cells
+    bad[0, n0 + 3] = -1.0                      # a negative density in solve 1
+    with pytest.raises(igks.IgksError) as e:
+        b.set_fields_all(bad)
+    assert e.value.code == igks.EINVAL
+    after = b.get_fields_all()
+    n1 = cases[1][0].n_cells
+    assert np.array_equal(after[:, n0:n0 + n1], before[:, n0:n0 + n1])
+    assert np.array_equal(after[:, :n0], bad[:, :n0])
+    assert np.array_equal(after[:, n0 + n1:], bad[:, n0 + n1:])
+    for c in ctxs:
+        c.destroy()
