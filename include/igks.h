@@ -72,7 +72,9 @@ typedef struct igks_options {
   int32_t device;         /* CUDA device ordinal */
   void* stream;           /* cudaStream_t to run on, or NULL for a stream of the context */
   int32_t check_every;    /* iterations between host checks of the stopping rule (>=1) */
-  int32_t use_graph;      /* capture one iteration as a CUDA graph and replay it */
+  int32_t use_graph;      /* capture one iteration (per group) as a CUDA graph and replay it;
+                             with 2 <= check_every <= 64 and no timing, also check_every
+                             iterations of every group as one graph, launched once per check */
   int32_t sweep_threads;  /* threads per block of the sweep kernels (0: default) */
   int32_t timing;         /* record CUDA events around every kernel (igks_kernel_times) */
   int32_t sweep_mode;     /* 0 automatic, 1 one block per solve walking its levels,
@@ -87,7 +89,7 @@ typedef struct igks_options {
   int32_t wait_limit;     /* tries of a device wait (the one-block-per-solve sweeps wait on an
                              mbarrier for each level's records) before it gives up: the solve
                              stops with state IGKS_TIMEOUT, its fields untouched, and
-                             igks_iterate returns IGKS_TIMEOUT (0: about a second) */
+                             igks_iterate returns IGKS_TIMEOUT (0: 2^24 tries, about 1.4 s) */
   int32_t starve_test;    /* test hook, 0 in use: 1 makes every forward sweep skip the copy of
                              its second level, so that the wait for it runs out */
   int32_t reserved[1];

@@ -1,5 +1,6 @@
 // igks_sweep.cu -- matrix-free LU-SGS forward and backward sweeps (Eq. 19-22 for the
-// mean flow, Eq. 31-32 for the SA variable) with the FP64 state update, in FP64 or FP32.
+// mean flow, Eq. 31-32 for the SA variable) with the FP64 state update, in FP64, FP32 or
+// double-float.
 //
 // Each sweep visits the cells in the dependency order of the sequential sweep of Eq. 20
 // (cell i needs its lower neighbours j < i forward, its upper neighbours j > i backward),
@@ -11,11 +12,13 @@
 // of active lanes, so the chain's FP64 instruction count sets the time of a level.
 //
 // Two schedules:
-//  - narrow: one block per solve walks its levels with a block barrier between them (for
-//    orderings with hundreds of thin levels). The increments of the last RING cells it
-//    produced stay in a shared-memory ring, so a cell usually reads its neighbours'
-//    increments from shared memory; its stencil (neighbour, ring slot, coefficients) is
-//    stored in sweep-position order so it is fetched without an indirection;
+//  - narrow: one block per solve (or a thread-block cluster) walks its levels with a
+//    barrier between them (for orderings with hundreds of thin levels). The increments of
+//    the last RING cells it produced stay in a shared-memory ring, so a cell usually reads
+//    its neighbours' increments from shared memory; its record (stencil neighbours, ring
+//    slots, coefficients and per-cell constants) is stored in sweep-position order, and a
+//    level's records are brought into shared memory by bulk copies on an mbarrier, a few
+//    levels ahead;
 //  - wide: one launch per level covering that level's cells of every solve (for low-depth
 //    orderings, e.g. multicolour, whose few levels hold thousands of cells each).
 #include <cooperative_groups.h>
